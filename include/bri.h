@@ -1,0 +1,154 @@
+/*
+ * bri.h -- C ABI of the GB300 (sm_103a) Brillouin-kernel overlap library.
+ *
+ * Operator definitions follow Duerr & Koutsou, "On the suitability of the
+ * Brillouin action as a kernel to the overlap procedure", arXiv:1701.00726:
+ *
+ *   D_bri = sum_mu gamma_mu nabla^iso_mu - (1/2) Delta^bri + m0
+ *           - (c_SW/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}          (Eq. def_bril)
+ *   D_wil = sum_mu gamma_mu nabla^std_mu - (1/2) Delta^std + m0 - clover
+ *                                                                   (Eq. def_wils)
+ *   D_ov  = rho [1 + gamma5 f_nn(H)],  H = gamma5 D_bri(m0 = -rho)  (Eq. def_over)
+ *   f_nn(x) = x [c0 + sum_i w_i / (x^2 + sigma_i)]                  (Eq. KLnn_parfrac)
+ *
+ * with a = 1.  Conventions shared by every call:
+ *
+ *   dims[4]   = {Lx, Ly, Lz, Lt}; site n = x + Lx*(y + Ly*(z + Lz*t)); V = Lx*Ly*Lz*Lt.
+ *   gauge U   = [V][mu=0..3 (x,y,z,t)][3][3] complex128 (re, im interleaved),
+ *               device memory; U_mu(n) transports from n+mu to n.
+ *   spinors   = [rhs][V][spin 4][colour 3] complex, interleaved (re, im), device
+ *               memory, complex128 when the precision is BRI_PREC_F64 and
+ *               complex64 (float) for BRI_PREC_F32 / BRI_PREC_F32_BF16.
+ *   gamma basis: chiral, gamma_k = [[0,-i s_k],[i s_k,0]], gamma_4 = [[0,1],[1,0]],
+ *               gamma5 = diag(1,1,-1,-1) (App. C counts gamma products as free
+ *               permutations in this basis).
+ *   offsets   : the 81 hypercube offsets d in {-1,0,1}^4 are numbered
+ *               nu-1 = (d_x+1) + 3(d_y+1) + 9(d_z+1) + 27(d_t+1); nu and 82-nu
+ *               are opposite and only nu = 1..40 are stored (App. C).
+ *
+ * Ownership: every array argument is caller-owned; the library never frees
+ * or retains caller memory.  The context owns the off-axis links, the clover
+ * field and solver workspaces.  All device work is issued on the context's
+ * stream; calls return once the work is enqueued unless documented otherwise
+ * (solvers synchronise the stream to test convergence).
+ *
+ * Errors: functions return BRI_OK (0), BRI_NOT_CONVERGED (1, output written)
+ * or a negative code; bri_last_error() gives a thread-local message.
+ */
+#ifndef BRI_H
+#define BRI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BRI_OK 0
+#define BRI_NOT_CONVERGED 1
+#define BRI_ERR_INVALID (-1)   /* bad argument (size, pointer, precision, order) */
+#define BRI_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define BRI_ERR_OOM (-3)       /* device allocation failed */
+#define BRI_ERR_NOLINKS (-4)   /* bri_build_links has not been called */
+#define BRI_ERR_NONFINITE (-5) /* a solver met a NaN/Inf in a reduction */
+
+/* Operator precision (spinor storage / link storage / accumulation). */
+#define BRI_PREC_F64 0       /* complex128 spinors, FP64 links, FP64 arithmetic */
+#define BRI_PREC_F32 1       /* complex64 spinors, FP32 links, FP32 accumulation */
+#define BRI_PREC_F32_BF16 2  /* complex64 spinors, BF16-stored links, FP32 accumulation */
+
+/* bri_create flags */
+#define BRI_ANTIPERIODIC_T 1 /* antiperiodic time direction (sign of U_t on the last slice) */
+
+/* Kenney-Laub family for kl_coeffs / solvers */
+#define BRI_KL_DIAGONAL 0 /* f_nn = g_{2n+1}: constant term + n shifts (Tab. 5) */
+#define BRI_KL_UPPER 1    /* f_{n-1,n} = g_{2n}: n shifts, no constant (Tab. 6) */
+
+#define BRI_MAX_SHIFTS 32
+
+typedef struct bri_ctx bri_ctx;
+
+/* Solver statistics (per call; per-rhs entries for rhs < 64). */
+typedef struct bri_stats {
+  int iterations;          /* multi-shift CG iterations (max over rhs) */
+  int matvecs;             /* applications of the kernel operator D or D^dagger */
+  int matvecs_f64;         /* of which in FP64 */
+  int refinements;         /* mixed precision: outer refinement rounds */
+  int n_shifts;            /* number of shifts solved */
+  double max_true_residual;/* max over rhs and shifts of ||b-(A+s_i)x_i||/||b|| (FP64),
+                              filled when want_true_residual != 0 */
+  double shift_residual[BRI_MAX_SHIFTS]; /* per shift, max over rhs */
+  int want_true_residual;  /* input: compute FP64 true residuals per shift */
+  int maxiter;             /* input: iteration cap (0 = default 20000) */
+  double seconds;          /* wall time of the call */
+} bri_stats;
+
+/* Create a context for one lattice.  dims: {Lx,Ly,Lz,Lt}, each >= 2.
+ * flags: BRI_ANTIPERIODIC_T or 0.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  Allocates nothing large until bri_build_links. */
+int bri_create(bri_ctx** ctx, const int dims[4], int flags, void* stream);
+void bri_destroy(bri_ctx* ctx);
+int bri_set_stream(bri_ctx* ctx, void* stream);
+
+/* Build the 40 stored path-averaged off-axis links W_nu(n), nu = 1..40
+ * (App. C: the average over the k! shortest paths of the link products, no
+ * SU(3) back-projection) in FP64, FP32 and BF16 storage, the thin-link copy
+ * used by wils_apply and, when c_sw != 0, the clover term
+ * -(c_sw/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu} with F the traceless
+ * anti-Hermitian part of the four-leaf clover divided by 8i.
+ * U: device, [V][4][3][3] complex128, read once; may be freed afterwards. */
+int bri_build_links(bri_ctx* ctx, const double* U, double c_sw);
+
+/* Export the stored links in the App. C layout [V][40][3][3] complex128
+ * (device pointer W, caller-allocated, 5760 bytes per site). */
+int bri_get_links(bri_ctx* ctx, double* W);
+
+/* y = D_bri x (dagger = 0) or D_bri^dagger x = gamma5 D_bri gamma5 x
+ * (dagger = 1) for nrhs right-hand sides, at bare mass m0 (Eq. def_bril;
+ * App. C: y(n) = sum over the 81 offsets of W_d(n) M_d x(n+d) with real
+ * stencil weights).  prec selects spinor dtype and link storage.  x and y
+ * must not alias. */
+int bri_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, double m0, int dagger, int prec);
+
+/* y = D_wil x or D_wil^dagger x (Eq. def_wils): 9-point stencil over the thin
+ * links plus the same clover term. */
+int wils_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, double m0, int dagger, int prec);
+
+/* Host-only: Kenney-Laub partial-fraction coefficients (Eq. KLnn_parfrac, Tab. 5;
+ * kind BRI_KL_UPPER: Tab. 6) of f(x/scale) = x [c0 + sum_i w_i/(x^2+sigma_i)],
+ * i = 0..n-1, shifts increasing.  Writes n entries into w and sigma. */
+int kl_coeffs(int n, int kind, double scale, double* c0, double* w, double* sigma);
+
+/* y = gamma5 f(H) x = D r(D^dagger D) x, H = gamma5 D_bri(m0 = -rho), with
+ * r(s) = c0 + sum_i w_i/(s+sigma_i) evaluated by one multi-shift CG
+ * (Sec. 3.3, Sec. 4.1) to relative residual tol on every shift.
+ * x, y: device complex128 [nrhs][V][4][3].  prec: BRI_PREC_F64 (all FP64) or
+ * BRI_PREC_F32 / BRI_PREC_F32_BF16 (FP32 inner solve with FP32 or BF16 links,
+ * FP64 reductions, FP64 defect-correction refinement to tol).  kind selects
+ * the Kenney-Laub family.  st may be NULL. */
+int sign_apply_multishift(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
+                          double rho, double scale, double tol, int prec, bri_stats* st);
+
+/* y = (1 - am/(2 rho)) rho (x + gamma5 f(H) x) + am x: the massless overlap
+ * (am = 0, Eq. def_over) or its traditional massive form
+ * (Eq. def_mass_traditional).  Same arguments as sign_apply_multishift. */
+int overlap_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
+                  double rho, double am, double scale, double tol, int prec, bri_stats* st);
+
+/* Profiling (tracing) of the stencil kernels.  When enabled, every launch of
+ * the Brillouin (op 0) or Wilson (op 1) stencil, including those issued inside
+ * the solvers, is bracketed by CUDA events on the context stream.
+ * bri_profile_read synchronises those events and returns, for one operator and
+ * precision, the launches, summed kernel milliseconds and site x rhs units
+ * processed since the previous read, then resets the counters. */
+int bri_profile_enable(bri_ctx* ctx, int enable);
+int bri_profile_read(bri_ctx* ctx, int op, int prec, long long* launches, double* ms, double* site_rhs);
+
+/* Process-wide number of CUDA kernels this library has launched so far. */
+long long bri_kernel_launches(void);
+
+/* Thread-local description of the last error (never NULL). */
+const char* bri_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BRI_H */

@@ -176,3 +176,86 @@ class DiracOperator:
     def normal(self, x):
         """A = D^dagger D."""
         return self.apply_dagger(self.apply(x))
+
+
+def _site_links_walk(u, site, d):
+    """W_d at one site by walking every shortest path with explicit coordinates."""
+    import itertools
+    import math
+    lt, lz, ly, lx = u.shape[:4]
+    dims = (lx, ly, lz, lt)
+
+    def link(pos, mu):
+        return u[pos[3] % lt, pos[2] % lz, pos[1] % ly, pos[0] % lx, mu]
+
+    nz = [mu for mu in range(4) if d[mu] != 0]
+    acc = np.zeros((3, 3), dtype=np.complex128)
+    for perm in itertools.permutations(nz):
+        pos = list(site)
+        prod = np.eye(3, dtype=np.complex128)
+        for mu in perm:
+            if d[mu] > 0:
+                prod = prod @ link(pos, mu)
+                pos[mu] += 1
+            else:
+                pos[mu] -= 1
+                prod = prod @ link(pos, mu).conj().T
+        acc += prod
+    return acc / math.factorial(len(nz)), dims
+
+
+def apply_at_sites(u, kind, m0, c_sw, x, sites, antiperiodic_t=False):
+    """y(n) = (D x)(n) at the listed sites only (x[rhs, t,z,y,x, 4, 3]).
+
+    A per-site restatement for sampled checks on lattices too large for the
+    whole-field oracle: transporters by explicit path walks, the clover term
+    from the four leaves at that site, the same stencil weights.
+    """
+    from .links import apply_time_bc
+    ub = apply_time_bc(u, antiperiodic_t)
+    lt, lz, ly, lx = ub.shape[:4]
+    mats = spin_matrices(kind, m0)
+    out = np.zeros((x.shape[0], len(sites), 4, 3), dtype=np.complex128)
+    g, _ = gammas()
+    for i, site in enumerate(sites):
+        sx, sy, sz, st = site
+        for idx, d in enumerate(all_offsets()):
+            m = mats[idx]
+            if not np.any(m):
+                continue
+            if idx == 40:
+                w = np.eye(3)
+            elif kind == "bri":
+                w, _ = _site_links_walk(ub, site, d)
+            else:
+                mu = [k for k in range(4) if d[k] != 0][0]
+                if d[mu] > 0:
+                    w = ub[st, sz, sy, sx, mu]
+                else:
+                    p = list(site)
+                    p[mu] -= 1
+                    w = ub[p[3] % lt, p[2] % lz, p[1] % ly, p[0] % lx, mu].conj().T
+            xs = x[:, (st + d[3]) % lt, (sz + d[2]) % lz, (sy + d[1]) % ly, (sx + d[0]) % lx]
+            out[:, i] += np.einsum("st,ab,rtb->rsa", m, w, xs)
+        if c_sw != 0.0:
+            cl = np.zeros((4, 3, 4, 3), dtype=np.complex128)
+
+            def L(pos, mu):
+                return ub[pos[3] % lt, pos[2] % lz, pos[1] % ly, pos[0] % lx, mu]
+
+            for mu in range(4):
+                for nu in range(mu + 1, 4):
+                    em = [int(k == mu) for k in range(4)]
+                    en = [int(k == nu) for k in range(4)]
+                    at = lambda a, b: [site[k] + a * em[k] + b * en[k] for k in range(4)]
+                    q = (L(at(0, 0), mu) @ L(at(1, 0), nu) @ L(at(0, 1), mu).conj().T @ L(at(0, 0), nu).conj().T
+                         + L(at(0, 0), nu) @ L(at(-1, 1), mu).conj().T @ L(at(-1, 0), nu).conj().T @ L(at(-1, 0), mu)
+                         + L(at(-1, 0), mu).conj().T @ L(at(-1, -1), nu).conj().T @ L(at(-1, -1), mu)
+                         @ L(at(0, -1), nu)
+                         + L(at(0, -1), nu).conj().T @ L(at(0, -1), mu) @ L(at(1, -1), nu) @ L(at(0, 0), mu).conj().T)
+                    f = (q - q.conj().T) / 8j
+                    f = f - np.trace(f) * np.eye(3) / 3.0
+                    sig = 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+                    cl += -0.5 * c_sw * np.einsum("st,ab->satb", sig, f)
+            out[:, i] += np.einsum("satb,rtb->rsa", cl, x[:, st, sz, sy, sx])
+    return out

@@ -1,0 +1,161 @@
+"""GB300-native Brillouin-kernel overlap operator (arXiv:1701.00726).
+
+The compute path is the CUDA library ``libbri.so`` behind the C ABI of
+``include/bri.h``; this package only marshals PyTorch tensors (device memory
+and streams) into it.  There is no CPU fallback: importing works without a
+GPU, but every operator call needs the built library and a CUDA device.
+
+Spinors are complex tensors of shape ``[nrhs, Lt, Lz, Ly, Lx, 4, 3]`` (or any
+shape with ``nrhs * V * 12`` elements, C-contiguous), complex128 for the FP64
+path and complex64 for the FP32 / BF16-link paths; gauge fields are complex128
+``[Lt, Lz, Ly, Lx, 4, 3, 3]``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KL_DIAGONAL, KL_UPPER, PREC_F32, PREC_F32_BF16, PREC_F64,
+                   BriError, BriStats, kl_coeffs)
+
+__all__ = ["Lattice", "kl_coeffs", "BriError", "BriStats", "PREC_F64", "PREC_F32", "PREC_F32_BF16",
+           "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Lattice:
+    """One lattice (dims = (Lx, Ly, Lz, Lt)) with its links, on the current CUDA device."""
+
+    def __init__(self, dims, antiperiodic_t=False, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise BriError("a CUDA device is required (libbri has no CPU path)")
+        self.lib = _lib.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.volume = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        handle = ctypes.c_void_p()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        flags = ANTIPERIODIC_T if antiperiodic_t else 0
+        _lib.check(self.lib.bri_create(ctypes.byref(handle), arr, flags, ctypes.c_void_p(self.stream.cuda_stream)),
+                   "bri_create")
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.bri_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ marshalling helpers
+    def _spinor(self, x, dtypes):
+        torch = _torch()
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise BriError("spinor must be a CUDA tensor")
+        if x.dtype not in dtypes:
+            raise BriError(f"spinor dtype {x.dtype} not in {dtypes}")
+        if not x.is_contiguous():
+            raise BriError("spinor must be contiguous")
+        per = self.volume * 12
+        if x.numel() == 0 or x.numel() % per:
+            raise BriError(f"spinor has {x.numel()} elements, not a multiple of V*12 = {per}")
+        return x.numel() // per
+
+    def build_links(self, u, c_sw=0.0):
+        torch = _torch()
+        if u.dtype != torch.complex128 or not u.is_cuda or not u.is_contiguous():
+            raise BriError("gauge field must be a contiguous complex128 CUDA tensor")
+        if u.numel() != self.volume * 36:
+            raise BriError("gauge field must have V*4*3*3 elements")
+        _lib.check(self.lib.bri_build_links(self._h, ctypes.c_void_p(u.data_ptr()), float(c_sw)), "bri_build_links")
+
+    def links(self):
+        """Stored off-axis links, complex128 [V, 40, 3, 3] (App. C layout)."""
+        torch = _torch()
+        w = torch.empty((self.volume, 40, 3, 3), dtype=torch.complex128, device="cuda")
+        _lib.check(self.lib.bri_get_links(self._h, ctypes.c_void_p(w.data_ptr())), "bri_get_links")
+        return w
+
+    def profile(self, enable=True):
+        _lib.check(self.lib.bri_profile_enable(self._h, int(bool(enable))), "bri_profile_enable")
+
+    def profile_read(self, op=0, prec=PREC_F32):
+        """(launches, kernel ms, site*rhs units) of one stencil since the last read."""
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        units = ctypes.c_double()
+        _lib.check(self.lib.bri_profile_read(self._h, int(op), int(prec), ctypes.byref(n), ctypes.byref(ms),
+                                             ctypes.byref(units)), "bri_profile_read")
+        return n.value, ms.value, units.value
+
+    @staticmethod
+    def kernel_launches():
+        return int(_lib.load().bri_kernel_launches())
+
+    @staticmethod
+    def _prec_for(x, bf16_links):
+        torch = _torch()
+        if x.dtype == torch.complex128:
+            return PREC_F64
+        return PREC_F32_BF16 if bf16_links else PREC_F32
+
+    def bri_apply(self, x, m0, dagger=False, bf16_links=False, out=None):
+        torch = _torch()
+        nrhs = self._spinor(x, (torch.complex128, torch.complex64))
+        y = torch.empty_like(x) if out is None else out
+        _lib.check(self.lib.bri_apply(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
+                                      float(m0), int(bool(dagger)), self._prec_for(x, bf16_links)), "bri_apply")
+        return y
+
+    def wils_apply(self, x, m0, dagger=False, out=None):
+        torch = _torch()
+        nrhs = self._spinor(x, (torch.complex128, torch.complex64))
+        y = torch.empty_like(x) if out is None else out
+        _lib.check(self.lib.wils_apply(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
+                                       float(m0), int(bool(dagger)), self._prec_for(x, False)), "wils_apply")
+        return y
+
+    def _solver_stats(self, want_true_residual, maxiter):
+        st = BriStats()
+        st.want_true_residual = int(bool(want_true_residual))
+        st.maxiter = int(maxiter)
+        return st
+
+    def sign_apply(self, x, n, rho=1.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL, scale=1.0,
+                   want_true_residual=False, maxiter=0, out=None):
+        """gamma5 f_nn(H) x, H = gamma5 D_bri(-rho); x complex128.  Returns (y, stats)."""
+        torch = _torch()
+        nrhs = self._spinor(x, (torch.complex128,))
+        y = torch.empty_like(x) if out is None else out
+        st = self._solver_stats(want_true_residual, maxiter)
+        rc = self.lib.sign_apply_multishift(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                            nrhs, int(n), int(kind), float(rho), float(scale), float(tol), int(prec),
+                                            ctypes.byref(st))
+        _lib.check(rc, "sign_apply_multishift")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return y, d
+
+    def overlap_apply(self, x, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL, scale=1.0,
+                      want_true_residual=False, maxiter=0, out=None):
+        """(1 - am/(2 rho)) D_ov x + am x with D_ov = rho (1 + gamma5 f_nn(H)).  Returns (y, stats)."""
+        torch = _torch()
+        nrhs = self._spinor(x, (torch.complex128,))
+        y = torch.empty_like(x) if out is None else out
+        st = self._solver_stats(want_true_residual, maxiter)
+        rc = self.lib.overlap_apply(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
+                                    int(n), int(kind), float(rho), float(am), float(scale), float(tol), int(prec),
+                                    ctypes.byref(st))
+        _lib.check(rc, "overlap_apply")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return y, d

@@ -1,0 +1,322 @@
+// C ABI entry points, context management and the host-side Kenney-Laub
+// coefficients.
+#include "internal.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+namespace bri {
+
+static thread_local std::string g_err = "no error";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t pool_event(bri_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_begin(bri_ctx* c, cudaStream_t s, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!c->prof_on) return BRI_OK;
+  *a = pool_event(c);
+  BRI_CUDA(cudaEventRecord(*a, s));
+  return BRI_OK;
+}
+
+int prof_end(bri_ctx* c, cudaStream_t s, cudaEvent_t a, int op, int prec, double units) {
+  if (!c->prof_on || !a) return BRI_OK;
+  cudaEvent_t b = pool_event(c);
+  BRI_CUDA(cudaEventRecord(b, s));
+  c->prof_pending.push_back(ProfRec{a, b, op, prec, units});
+  return BRI_OK;
+}
+
+static int prof_collect(bri_ctx* c) {
+  for (auto& r : c->prof_pending) {
+    BRI_CUDA(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    BRI_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    c->prof_launches[r.op][r.prec] += 1;
+    c->prof_ms[r.op][r.prec] += ms;
+    c->prof_units[r.op][r.prec] += r.units;
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+  return BRI_OK;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? BRI_ERR_OOM : BRI_ERR_CUDA;
+}
+
+// Eq. KLnn_parfrac: g_{2n+1}(x) = x/(2n+1) sum_{i=0}^{n} (2 - delta_{in}) / (sin^2 t_i + cos^2 t_i x^2),
+// t_i = (2i+1) pi/(4n+2); the i = n term is the constant.  Upper diagonal (Sec. 3.3):
+// g_{2n}(x) = (x/n) sum_{i<n} 1/(sin^2 t_i + cos^2 t_i x^2), t_i = (2i+1) pi/(4n).
+// With a scale s, f(x/s) = x [c0/s + sum (w_i s)/(x^2 + sigma_i s^2)].
+int kl_host(int n, int kind, double scale, double* c0, double* w, double* sigma) {
+  if (n < 1 || n > BRI_MAX_SHIFTS) {
+    set_error("kl_coeffs: order n must be in [1, 32]");
+    return BRI_ERR_INVALID;
+  }
+  if (!(scale > 0.0) || !std::isfinite(scale)) {
+    set_error("kl_coeffs: scale must be positive");
+    return BRI_ERR_INVALID;
+  }
+  if (!c0 || !w || !sigma) {
+    set_error("kl_coeffs: null output pointer");
+    return BRI_ERR_INVALID;
+  }
+  const double pi = 3.14159265358979323846;
+  if (kind == BRI_KL_DIAGONAL) {
+    for (int i = 0; i < n; ++i) {
+      const double th = (2 * i + 1) * pi / (4.0 * n + 2.0);
+      const double cs = std::cos(th), sn = std::sin(th);
+      sigma[i] = (sn / cs) * (sn / cs) * scale * scale;
+      w[i] = 2.0 / ((2.0 * n + 1.0) * cs * cs) * scale;
+    }
+    *c0 = 1.0 / ((2.0 * n + 1.0) * scale);
+  } else if (kind == BRI_KL_UPPER) {
+    for (int i = 0; i < n; ++i) {
+      const double th = (2 * i + 1) * pi / (4.0 * n);
+      const double cs = std::cos(th), sn = std::sin(th);
+      sigma[i] = (sn / cs) * (sn / cs) * scale * scale;
+      w[i] = 1.0 / (n * cs * cs) * scale;
+    }
+    *c0 = 0.0;
+  } else {
+    set_error("kl_coeffs: kind must be BRI_KL_DIAGONAL or BRI_KL_UPPER");
+    return BRI_ERR_INVALID;
+  }
+  return BRI_OK;
+}
+
+}  // namespace bri
+
+using namespace bri;
+
+extern "C" {
+
+const char* bri_last_error(void) { return g_err.c_str(); }
+
+int bri_create(bri_ctx** out, const int dims[4], int flags, void* stream) {
+  if (!out || !dims) {
+    set_error("bri_create: null argument");
+    return BRI_ERR_INVALID;
+  }
+  *out = nullptr;
+  int64_t V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (dims[mu] < 2 || dims[mu] > 4096) {
+      set_error("bri_create: every extent must be in [2, 4096]");
+      return BRI_ERR_INVALID;
+    }
+    V *= dims[mu];
+  }
+  if (V > (int64_t(1) << 31) / 40) {
+    set_error("bri_create: lattice volume too large for one device");
+    return BRI_ERR_INVALID;
+  }
+  if (flags & ~BRI_ANTIPERIODIC_T) {
+    set_error("bri_create: unknown flag");
+    return BRI_ERR_INVALID;
+  }
+  bri_ctx* c = new bri_ctx();
+  for (int mu = 0; mu < 4; ++mu) c->g.L[mu] = dims[mu];
+  c->g.V = V;
+  c->g.str[0] = 1;
+  c->g.str[1] = dims[0];
+  c->g.str[2] = (int64_t)dims[0] * dims[1];
+  c->g.str[3] = (int64_t)dims[0] * dims[1] * dims[2];
+  c->flags = flags;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaMallocHost(&c->host_pinned, 1 << 16);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "bri_create: cudaMallocHost");
+  }
+  *out = c;
+  return BRI_OK;
+}
+
+void bri_destroy(bri_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(c->W64);
+  cudaFree(c->W32);
+  cudaFree(c->W16);
+  cudaFree(c->U64);
+  cudaFree(c->U32);
+  cudaFree(c->C64);
+  cudaFree(c->C32);
+  for (auto& r : c->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+  cudaFree(c->ws.ptr);
+  cudaFree(c->ws_small.ptr);
+  cudaFreeHost(c->host_pinned);
+  cudaGetLastError();
+  delete c;
+}
+
+int bri_set_stream(bri_ctx* c, void* stream) {
+  if (!c) {
+    set_error("bri_set_stream: null context");
+    return BRI_ERR_INVALID;
+  }
+  c->stream = (cudaStream_t)stream;
+  return BRI_OK;
+}
+
+int bri_build_links(bri_ctx* c, const double* U, double c_sw) {
+  if (!c || !U) {
+    set_error("bri_build_links: null argument");
+    return BRI_ERR_INVALID;
+  }
+  if (!std::isfinite(c_sw)) {
+    set_error("bri_build_links: c_sw must be finite");
+    return BRI_ERR_INVALID;
+  }
+  return launch_build_links(c, U, c_sw);
+}
+
+int bri_get_links(bri_ctx* c, double* W) {
+  if (!c || !W) {
+    set_error("bri_get_links: null argument");
+    return BRI_ERR_INVALID;
+  }
+  if (!c->have_links) {
+    set_error("bri_get_links: call bri_build_links first");
+    return BRI_ERR_NOLINKS;
+  }
+  return launch_export_links(c, W);
+}
+
+static int check_apply(bri_ctx* c, void* y, const void* x, int nrhs, int prec, const char* who) {
+  if (!c || !y || !x) {
+    set_error(std::string(who) + ": null argument");
+    return BRI_ERR_INVALID;
+  }
+  if (!c->have_links) {
+    set_error(std::string(who) + ": call bri_build_links first");
+    return BRI_ERR_NOLINKS;
+  }
+  if (nrhs < 1 || nrhs > 65535) {
+    set_error(std::string(who) + ": nrhs must be in [1, 65535]");
+    return BRI_ERR_INVALID;
+  }
+  if (prec != BRI_PREC_F64 && prec != BRI_PREC_F32 && prec != BRI_PREC_F32_BF16) {
+    set_error(std::string(who) + ": unknown precision");
+    return BRI_ERR_INVALID;
+  }
+  if (y == x) {
+    set_error(std::string(who) + ": x and y must not alias");
+    return BRI_ERR_INVALID;
+  }
+  if (((uintptr_t)x | (uintptr_t)y) & 15) {
+    set_error(std::string(who) + ": spinor pointers must be 16-byte aligned");
+    return BRI_ERR_INVALID;
+  }
+  return BRI_OK;
+}
+
+int bri_apply(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec) {
+  int rc = check_apply(c, y, x, nrhs, prec, "bri_apply");
+  if (rc) return rc;
+  return dirac_bri(c, y, x, nrhs, m0, dagger ? 1 : 0, prec, c->stream);
+}
+
+int wils_apply(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec) {
+  int rc = check_apply(c, y, x, nrhs, prec, "wils_apply");
+  if (rc) return rc;
+  return dirac_wil(c, y, x, nrhs, m0, dagger ? 1 : 0, prec, c->stream);
+}
+
+int kl_coeffs(int n, int kind, double scale, double* c0, double* w, double* sigma) {
+  return kl_host(n, kind, scale, c0, w, sigma);
+}
+
+static int check_solver(bri_ctx* c, void* y, const void* x, int nrhs, int n, double rho, double tol, int prec,
+                        const char* who) {
+  int rc = check_apply(c, y, x, nrhs, prec, who);
+  if (rc) return rc;
+  if (n < 1 || n > BRI_MAX_SHIFTS) {
+    set_error(std::string(who) + ": KL order n must be in [1, 32]");
+    return BRI_ERR_INVALID;
+  }
+  if (!(rho > 0.0 && rho < 2.0)) {
+    set_error(std::string(who) + ": rho must be in (0, 2)");
+    return BRI_ERR_INVALID;
+  }
+  if (!(tol > 0.0 && tol < 1.0)) {
+    set_error(std::string(who) + ": tol must be in (0, 1)");
+    return BRI_ERR_INVALID;
+  }
+  return BRI_OK;
+}
+
+int sign_apply_multishift(bri_ctx* c, void* y, const void* x, int nrhs, int n, int kind, double rho, double scale,
+                          double tol, int prec, bri_stats* st) {
+  int rc = check_solver(c, y, x, nrhs, n, rho, tol, prec, "sign_apply_multishift");
+  if (rc) return rc;
+  return sign_apply(c, (double2*)y, (const double2*)x, nrhs, n, kind, rho, scale, tol, prec, 1.0, 0.0, st);
+}
+
+int overlap_apply(bri_ctx* c, void* y, const void* x, int nrhs, int n, int kind, double rho, double am,
+                  double scale, double tol, int prec, bri_stats* st) {
+  int rc = check_solver(c, y, x, nrhs, n, rho, tol, prec, "overlap_apply");
+  if (rc) return rc;
+  if (!std::isfinite(am) || am >= 2.0 * rho) {
+    set_error("overlap_apply: the traditional massive form needs am < 2 rho");
+    return BRI_ERR_INVALID;
+  }
+  // (1 - am/(2 rho)) rho (x + s) + am x
+  const double k = (1.0 - am / (2.0 * rho)) * rho;
+  return sign_apply(c, (double2*)y, (const double2*)x, nrhs, n, kind, rho, scale, tol, prec, k, k + am, st);
+}
+
+int bri_profile_enable(bri_ctx* c, int enable) {
+  if (!c) {
+    set_error("bri_profile_enable: null context");
+    return BRI_ERR_INVALID;
+  }
+  c->prof_on = enable != 0;
+  return BRI_OK;
+}
+
+int bri_profile_read(bri_ctx* c, int op, int prec, long long* launches, double* ms, double* site_rhs) {
+  if (!c || op < 0 || op > 1 || prec < 0 || prec > 2 || !launches || !ms || !site_rhs) {
+    set_error("bri_profile_read: bad argument");
+    return BRI_ERR_INVALID;
+  }
+  int rc = prof_collect(c);
+  if (rc) return rc;
+  *launches = c->prof_launches[op][prec];
+  *ms = c->prof_ms[op][prec];
+  *site_rhs = c->prof_units[op][prec];
+  c->prof_launches[op][prec] = 0;
+  c->prof_ms[op][prec] = 0.0;
+  c->prof_units[op][prec] = 0.0;
+  return BRI_OK;
+}
+
+long long bri_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal declarations shared by the CUDA translation units of libbri.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/bri.h"
+
+namespace bri {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+#define BRI_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return ::bri::cuda_fail(e_, #call); \
+  } while (0)
+
+#define BRI_LAUNCH_CHECK(where)                          \
+  do {                                                   \
+    cudaError_t e_ = cudaGetLastError();                 \
+    if (e_ != cudaSuccess) return ::bri::cuda_fail(e_, where); \
+  } while (0)
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  int L[4];      // Lx, Ly, Lz, Lt
+  int64_t V;     // volume
+  int64_t str[4];// site strides 1, Lx, Lx*Ly, Lx*Ly*Lz
+};
+
+// ---------------------------------------------------------------- context
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Event-bracketed stencil launches (profiling), per operator x precision.
+struct ProfRec {
+  cudaEvent_t a, b;
+  int op, prec;
+  double units;
+};
+
+void note_launch();
+
+}  // namespace bri
+
+#include <vector>
+
+struct bri_ctx {
+  bri::Geom g;
+  int flags = 0;
+  cudaStream_t stream = nullptr;
+  bool have_links = false;
+  bool have_clover = false;
+  double c_sw = 0.0;
+  // Stored off-axis links, structure-of-arrays [40][9][V] complex (FP64 /
+  // FP32 / BF16): element (nu, e, n) sits at (nu*9 + e)*V + n so that a warp
+  // of consecutive sites reads one contiguous 256/512/128-byte segment.
+  double2* W64 = nullptr;
+  float2* W32 = nullptr;
+  __nv_bfloat162* W16 = nullptr;
+  // Thin links with the time boundary applied, [4][9][V] (Wilson kernel).
+  double2* U64 = nullptr;
+  float2* U32 = nullptr;
+  // Clover: two Hermitian 6x6 chiral blocks per site, packed as 72 reals:
+  // [block][36][V]: 6 diagonal reals, then 15 upper off-diagonal complex.
+  double* C64 = nullptr;
+  float* C32 = nullptr;
+  // solver workspace (grown on demand)
+  bri::Workspace ws;
+  bri::Workspace ws_small;
+  void* host_pinned = nullptr;
+  // profiling of stencil launches
+  bool prof_on = false;
+  std::vector<bri::ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  long long prof_launches[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  double prof_ms[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  double prof_units[2][3] = {{0, 0, 0}, {0, 0, 0}};
+};
+
+namespace bri {
+
+// ---------------------------------------------------------------- kernels (host launchers)
+int launch_build_links(bri_ctx* c, const double* U, double c_sw);
+int launch_export_links(bri_ctx* c, double* W);
+
+// spinor precision dispatch for the stencils
+int dirac_bri(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
+              cudaStream_t s);
+int dirac_wil(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
+              cudaStream_t s);
+
+// host-side KL coefficients
+int kl_host(int n, int kind, double scale, double* c0, double* w, double* sigma);
+
+// solvers
+int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho,
+               double scale, double tol, int prec, double out_scale, double b_coeff,
+               bri_stats* st);
+
+// profiling brackets (no-ops unless enabled on the context)
+int prof_begin(bri_ctx* c, cudaStream_t s, cudaEvent_t* a);
+int prof_end(bri_ctx* c, cudaStream_t s, cudaEvent_t a, int op, int prec, double units);
+
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace bri

@@ -1,0 +1,629 @@
+// Multi-shift CG on A = D^dagger D and the Kenney-Laub sign function / overlap.
+//
+// Sec. 3.3 and App. B: f_nn(H) b = H r(H^2) b, r(s) = c0 + sum_i w_i/(s + sigma_i),
+// so with H = gamma5 D (gamma5-hermitian kernel at m0 = -rho, Eq. def_over)
+//   gamma5 f(H) b = D (c0 b + sum_i w_i x_i),   x_i = (D^dagger D + sigma_i)^{-1} b.
+// All x_i come out of one Krylov space (multi-shift CG, Jegerlehner form):
+// the base system is the smallest shift, the others follow from the collinear
+// residual recurrences
+//   zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+//                [alpha_k beta_{k-1} (zeta_{k-1} - zeta_k) + zeta_{k-1} alpha_{k-1} (1 + delta alpha_k)]
+//   alpha^i_k = alpha_k zeta_{k+1}/zeta_k,  beta^i_k = beta_k (zeta_{k+1}/zeta_k)^2.
+//
+// Device-resident scalars: the CG coefficients of every system live in device
+// memory and are advanced by one-block "scalar" kernels, so the host only
+// polls a done flag every few iterations.  Global inner products are FP64
+// block partials summed in a fixed order (deterministic).
+//
+// Mixed precision (prec = F32 or F32/BF16 links): the multi-shift solve runs
+// with FP32 vectors and operator (FP64 scalars and reductions) to ~1e-6, then
+// each shift is refined by defect correction: the FP64 residual
+// r_i = b - (A + sigma_i) X_i is computed with the FP64 operator and an FP32 CG
+// correction (A + sigma_i) e_i = r_i is added in FP64, until every shift has
+// ||r_i|| <= tol ||b||.  All corrections of one round run as one batched CG
+// with a per-system shift.
+#include "internal.cuh"
+#include "cplx.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+namespace bri {
+namespace {
+
+constexpr int NS = BRI_MAX_SHIFTS;
+constexpr int RED_THREADS = 256;
+
+struct MsState {
+  double rr, bnorm2, pq, alpha, alpha_prev, beta_prev, tol2;
+  double sig_base;
+  double delta[NS];
+  double zeta[NS], zeta_prev[NS], zeta_next[NS];
+  double a_s[NS], b_s[NS];
+  int active[NS];
+  int nshift, done, iters, maxiter, error;
+};
+
+template <typename R> struct P2;
+template <> struct P2<float> { using T = float2; };
+template <> struct P2<double> { using T = double2; };
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    r = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// ----------------------------------------------------------------- vector kernels
+// Vectors are flat arrays of n2 pairs (re, im) per system; system s at s*n2.
+
+// r = b, p_i = b (all shifts), x_i = 0, partial ||b||^2
+template <typename R>
+__global__ void k_init(int64_t n2, int nsys, int nshift, const typename P2<R>::T* __restrict__ b,
+                       typename P2<R>::T* r, typename P2<R>::T* p, typename P2<R>::T* x, double* part) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    T v = b[s * n2 + i];
+    r[s * n2 + i] = v;
+    for (int k = 0; k < nshift; ++k) {
+      p[((int64_t)k * nsys + s) * n2 + i] = v;
+      x[((int64_t)k * nsys + s) * n2 + i] = T{0, 0};
+    }
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// q += sigma_base p_0 ; partial Re <p_0, q>
+template <typename R>
+__global__ void k_shift_dot(int64_t n2, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ p0,
+                            typename P2<R>::T* q, double* part) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  if (st[s].done) return;
+  const R sb = (R)st[s].sig_base;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    T pv = p0[s * n2 + i];
+    T qv = q[s * n2 + i];
+    qv.x = fma(sb, pv.x, qv.x);
+    qv.y = fma(sb, pv.y, qv.y);
+    q[s * n2 + i] = qv;
+    acc += (double)pv.x * qv.x + (double)pv.y * qv.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// x_i += alpha_i p_i (active i); r -= alpha q; partial ||r||^2
+template <typename R>
+__global__ void k_update_xr(int64_t n2, int nsys, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ q,
+                            typename P2<R>::T* r, const typename P2<R>::T* __restrict__ p, typename P2<R>::T* x,
+                            double* part) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  if (st[s].done) return;
+  const int nshift = st[s].nshift;
+  const R alpha = (R)st[s].alpha;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nshift; ++k) {
+      if (!st[s].active[k]) continue;
+      const R a = (R)st[s].a_s[k];
+      const int64_t o = ((int64_t)k * nsys + s) * n2 + i;
+      T pv = p[o], xv = x[o];
+      xv.x = fma(a, pv.x, xv.x);
+      xv.y = fma(a, pv.y, xv.y);
+      x[o] = xv;
+    }
+    T rv = r[s * n2 + i], qv = q[s * n2 + i];
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    r[s * n2 + i] = rv;
+    acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// p_i = zeta_i r + beta_i p_i (active i)
+template <typename R>
+__global__ void k_update_p(int64_t n2, int nsys, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ r,
+                           typename P2<R>::T* p) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  const int nshift = st[s].nshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    T rv = r[s * n2 + i];
+    for (int k = 0; k < nshift; ++k) {
+      if (!st[s].active[k]) continue;
+      const R z = (R)st[s].zeta[k], bt = (R)st[s].b_s[k];
+      const int64_t o = ((int64_t)k * nsys + s) * n2 + i;
+      T pv = p[o];
+      pv.x = fma(bt, pv.x, z * rv.x);
+      pv.y = fma(bt, pv.y, z * rv.y);
+      p[o] = pv;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- scalar kernels (one block per system)
+__global__ void k_scalar_init(MsState* st, const double* part, int nblk) {
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[s * nblk + i];
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) {
+    MsState& S = st[s];
+    S.rr = t;
+    S.bnorm2 = t;
+    S.alpha_prev = 1.0;
+    S.beta_prev = 0.0;
+    S.iters = 0;
+    S.error = 0;
+    for (int k = 0; k < S.nshift; ++k) {
+      S.zeta[k] = 1.0;
+      S.zeta_prev[k] = 1.0;
+      S.active[k] = 1;
+    }
+    S.done = (t == 0.0) ? 1 : 0;
+    if (t == 0.0)
+      for (int k = 0; k < S.nshift; ++k) S.active[k] = 0;
+  }
+}
+
+__global__ void k_scalar_alpha(MsState* st, const double* part, int nblk) {
+  const int s = blockIdx.x;
+  if (st[s].done) return;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[s * nblk + i];
+  double pq = block_sum(acc);
+  if (threadIdx.x == 0) {
+    MsState& S = st[s];
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      S.error = 1;
+      S.done = 1;
+      for (int k = 0; k < S.nshift; ++k) S.active[k] = 0;
+      return;
+    }
+    const double alpha = S.rr / pq;
+    S.pq = pq;
+    S.alpha = alpha;
+    for (int k = 0; k < S.nshift; ++k) {
+      const double den = alpha * S.beta_prev * (S.zeta_prev[k] - S.zeta[k]) +
+                         S.zeta_prev[k] * S.alpha_prev * (1.0 + S.delta[k] * alpha);
+      const double zn = S.zeta[k] * S.zeta_prev[k] * S.alpha_prev / den;
+      S.zeta_next[k] = zn;
+      S.a_s[k] = alpha * zn / S.zeta[k];
+    }
+  }
+}
+
+__global__ void k_scalar_beta(MsState* st, const double* part, int nblk) {
+  const int s = blockIdx.x;
+  if (st[s].done) return;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[s * nblk + i];
+  double rr = block_sum(acc);
+  if (threadIdx.x == 0) {
+    MsState& S = st[s];
+    if (!isfinite(rr)) {
+      S.error = 1;
+      S.done = 1;
+      for (int k = 0; k < S.nshift; ++k) S.active[k] = 0;
+      return;
+    }
+    const double beta = rr / S.rr;
+    for (int k = 0; k < S.nshift; ++k) {
+      const double ratio = S.zeta_next[k] / S.zeta[k];
+      S.b_s[k] = beta * ratio * ratio;
+      S.zeta_prev[k] = S.zeta[k];
+      S.zeta[k] = S.zeta_next[k];
+    }
+    S.alpha_prev = S.alpha;
+    S.beta_prev = beta;
+    S.rr = rr;
+    S.iters += 1;
+    for (int k = 0; k < S.nshift; ++k)
+      if (S.active[k] && S.zeta[k] * S.zeta[k] * rr <= S.tol2 * S.bnorm2) S.active[k] = 0;
+    if (!S.active[0] || S.iters >= S.maxiter) {
+      // p updates of the still-active (larger) shifts are skipped once the base stops
+      S.done = 1;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- precision / algebra helpers
+template <typename A, typename B>
+__global__ void k_convert(int64_t n, const A* __restrict__ in, B* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
+// X (FP64) += (double) e (FP32), n reals
+__global__ void k_accumulate(int64_t n, double* X, const float* __restrict__ e) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    X[i] += (double)e[i];
+}
+
+// res = b - q - sigma X ; partial ||res||^2 ; q is (A X)
+__global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
+                           const double* __restrict__ X, double sigma, double* res, double* part) {
+  const int s = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = s * n + i;
+    double v = b[o] - q[o] - sigma * X[o];
+    if (res) res[o] = v;
+    acc += v * v;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_sum_partials(const double* part, int nblk, double* out) {
+  const int s = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += part[s * nblk + i];
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) out[s] = t;
+}
+
+// acc = c0 b + sum_i w_i X_i   (FP64, X = [nshift][nsys][n])
+__global__ void k_rational(int64_t n, int nsys, int nshift, double c0, const double* __restrict__ w,
+                           const double* __restrict__ b, const double* __restrict__ X, double* out) {
+  const int s = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = c0 * b[s * n + i];
+    for (int k = 0; k < nshift; ++k) v += w[k] * X[((int64_t)k * nsys + s) * n + i];
+    out[s * n + i] = v;
+  }
+}
+
+// y = cb b + cz z
+__global__ void k_axpby(int64_t n, double cb, const double* __restrict__ b, double cz, const double* __restrict__ z,
+                        double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = cb * b[i] + cz * z[i];
+}
+
+int grid_for(int64_t n, int nsys) {
+  int64_t b = (n + RED_THREADS - 1) / RED_THREADS;
+  int64_t cap = std::max<int64_t>(1, 2048 / std::max(1, nsys));
+  return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// ----------------------------------------------------------------- device memory from the stream-ordered pool
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  int alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    if (p) {
+      cudaFreeAsync(p, s);
+      p = nullptr;
+    }
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      set_error(std::string("cudaMallocAsync failed: ") + cudaGetErrorString(e));
+      return BRI_ERR_OOM;
+    }
+    return BRI_OK;
+  }
+  template <typename T> T* as() const { return (T*)p; }
+};
+
+void configure_pool_once() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done = true;
+}
+
+// Operator application for the solver: out = D in (dagger 0) / D^dagger in.
+template <typename R> int op_prec(int prec);
+template <> int op_prec<double>(int) { return BRI_PREC_F64; }
+template <> int op_prec<float>(int prec) { return prec == BRI_PREC_F32_BF16 ? BRI_PREC_F32_BF16 : BRI_PREC_F32; }
+
+struct Counters {
+  int matvecs = 0, matvecs64 = 0;
+};
+
+// Solve (A + sig[s][k]) x[k][s] = b[s] for nsys systems with nshift shifts each.
+// sig: host [nsys][nshift], increasing within a system.
+template <typename R>
+int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, const double* sig, const R* b, R* x,
+                     double tol, int maxiter, int* iters_out, Counters* cnt) {
+  using T = typename P2<R>::T;
+  cudaStream_t st = c->stream;
+  const int64_t n2 = c->g.V * 12;  // complex pairs per system
+  const int nblk = grid_for(n2, nsys);
+  const int oprec = op_prec<R>(prec);
+  DevBuf br, bp, bt, bq, bst, bpart;
+  int rc;
+  if ((rc = br.alloc(sizeof(T) * n2 * nsys, st))) return rc;
+  if ((rc = bp.alloc(sizeof(T) * n2 * nsys * nshift, st))) return rc;
+  if ((rc = bt.alloc(sizeof(T) * n2 * nsys, st))) return rc;
+  if ((rc = bq.alloc(sizeof(T) * n2 * nsys, st))) return rc;
+  if ((rc = bst.alloc(sizeof(MsState) * nsys, st))) return rc;
+  if ((rc = bpart.alloc(sizeof(double) * nblk * nsys, st))) return rc;
+  T* r = br.as<T>();
+  T* p = bp.as<T>();
+  T* t = bt.as<T>();
+  T* q = bq.as<T>();
+  MsState* S = bst.as<MsState>();
+  double* part = bpart.as<double>();
+
+  std::vector<MsState> hs(nsys);
+  for (int s = 0; s < nsys; ++s) {
+    MsState& h = hs[s];
+    memset(&h, 0, sizeof(h));
+    h.nshift = nshift;
+    h.sig_base = sig[s * nshift];
+    for (int k = 0; k < nshift; ++k) h.delta[k] = sig[s * nshift + k] - h.sig_base;
+    h.tol2 = tol * tol;
+    h.maxiter = maxiter;
+  }
+  BRI_CUDA(cudaMemcpyAsync(S, hs.data(), sizeof(MsState) * nsys, cudaMemcpyHostToDevice, st));
+  dim3 vg(nblk, nsys);
+  k_init<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, nshift, (const T*)b, r, p, (T*)x, part); note_launch();
+  k_scalar_init<<<nsys, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+  BRI_LAUNCH_CHECK("multishift init");
+
+  int* hdone = (int*)c->host_pinned;  // pinned scratch, >= 4 KB
+  const int check_every = 8;
+  int it = 0;
+  bool all_done = false;
+  while (!all_done && it < maxiter) {
+    for (int j = 0; j < check_every && it < maxiter; ++j, ++it) {
+      if ((rc = dirac_bri(c, t, p, nsys, m0, 0, oprec, st))) return rc;
+      if ((rc = dirac_bri(c, q, t, nsys, m0, 1, oprec, st))) return rc;
+      cnt->matvecs += 2;
+      if (sizeof(R) == 8) cnt->matvecs64 += 2;
+      k_shift_dot<R><<<vg, RED_THREADS, 0, st>>>(n2, S, p, q, part); note_launch();
+      k_scalar_alpha<<<nsys, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      k_update_xr<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, S, q, r, p, (T*)x, part); note_launch();
+      k_scalar_beta<<<nsys, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      k_update_p<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, S, r, p); note_launch();
+    }
+    BRI_LAUNCH_CHECK("multishift iteration");
+    // poll the done flags of all systems
+    for (int s = 0; s < nsys; ++s)
+      BRI_CUDA(cudaMemcpyAsync(hdone + 2 * s, &S[s].done, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    BRI_CUDA(cudaStreamSynchronize(st));
+    all_done = true;
+    for (int s = 0; s < nsys; ++s) all_done = all_done && hdone[2 * s];
+  }
+  BRI_CUDA(cudaMemcpyAsync(hs.data(), S, sizeof(MsState) * nsys, cudaMemcpyDeviceToHost, st));
+  BRI_CUDA(cudaStreamSynchronize(st));
+  int maxit = 0, err = 0, notconv = 0;
+  for (int s = 0; s < nsys; ++s) {
+    maxit = std::max(maxit, hs[s].iters);
+    err |= hs[s].error;
+    if (hs[s].active[0] && !hs[s].error) notconv = 1;
+  }
+  *iters_out = maxit;
+  if (err) {
+    set_error("multi-shift CG: non-finite or non-positive curvature in a reduction");
+    return BRI_ERR_NONFINITE;
+  }
+  return notconv ? BRI_NOT_CONVERGED : BRI_OK;
+}
+
+// ||b - (A + sigma) X||^2 per system for one shift (FP64 operator); res may be null.
+int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X, double sigma, double* res,
+               double* tmp1, double* tmp2, double* part, double* dsum, double* hsum, Counters* cnt) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->g.V * 24;
+  int rc;
+  if ((rc = dirac_bri(c, tmp1, X, nsys, m0, 0, BRI_PREC_F64, st))) return rc;
+  if ((rc = dirac_bri(c, tmp2, tmp1, nsys, m0, 1, BRI_PREC_F64, st))) return rc;
+  cnt->matvecs += 2;
+  cnt->matvecs64 += 2;
+  const int nblk = grid_for(n / 2, nsys);
+  k_residual<<<dim3(nblk, nsys), RED_THREADS, 0, st>>>(n, b, tmp2, X, sigma, res, part); note_launch();
+  k_sum_partials<<<nsys, RED_THREADS, 0, st>>>(part, nblk, dsum); note_launch();
+  BRI_LAUNCH_CHECK("residual64");
+  BRI_CUDA(cudaMemcpyAsync(hsum, dsum, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  BRI_CUDA(cudaStreamSynchronize(st));
+  return BRI_OK;
+}
+
+}  // namespace
+
+int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho, double scale,
+               double tol, int prec, double out_scale, double b_coeff, bri_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  configure_pool_once();
+  cudaStream_t st = c->stream;
+  const int64_t nreal = c->g.V * 24;
+  const double m0 = -rho;
+  double c0, w[NS], sig[NS];
+  int rc = kl_host(n, kind, scale, &c0, w, sig);
+  if (rc) return rc;
+  const int maxiter = (stats && stats->maxiter > 0) ? stats->maxiter : 20000;
+  Counters cnt;
+  int iters = 0, refinements = 0;
+  const double* b = (const double*)x;
+
+  std::vector<double> sig_all((size_t)nrhs * n);
+  for (int s = 0; s < nrhs; ++s)
+    for (int k = 0; k < n; ++k) sig_all[(size_t)s * n + k] = sig[k];
+
+  DevBuf bX;
+  if ((rc = bX.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
+  double* X = bX.as<double>();
+  int solve_rc = BRI_OK;
+
+  if (prec == BRI_PREC_F64) {
+    solve_rc = multishift_solve<double>(c, prec, m0, nrhs, n, sig_all.data(), b, X, tol, maxiter, &iters, &cnt);
+    if (solve_rc < 0) return solve_rc;
+  } else if (prec == BRI_PREC_F32 || prec == BRI_PREC_F32_BF16) {
+    // phase 1: FP32 multi-shift
+    DevBuf bb32, bx32;
+    if ((rc = bb32.alloc(sizeof(float) * nreal * nrhs, st))) return rc;
+    if ((rc = bx32.alloc(sizeof(float) * nreal * nrhs * n, st))) return rc;
+    k_convert<double, float><<<1024, 256, 0, st>>>(nreal * nrhs, b, bb32.as<float>()); note_launch();
+    const double tol1 = std::max(tol, 1e-6);
+    int it1 = 0;
+    rc = multishift_solve<float>(c, prec, m0, nrhs, n, sig_all.data(), bb32.as<float>(), bx32.as<float>(), tol1,
+                                 maxiter, &it1, &cnt);
+    if (rc < 0) return rc;
+    iters = it1;
+    k_convert<float, double><<<1024, 256, 0, st>>>(nreal * nrhs * n, bx32.as<float>(), X); note_launch();
+    BRI_LAUNCH_CHECK("convert");
+    // phase 2: defect correction per shift
+    DevBuf btmp1, btmp2, bpart, bdsum, bres;
+    if ((rc = btmp1.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+    if ((rc = btmp2.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+    const int nblk_r = grid_for(nreal / 2, nrhs);
+    if ((rc = bpart.alloc(sizeof(double) * nblk_r * nrhs, st))) return rc;
+    if ((rc = bdsum.alloc(sizeof(double) * nrhs, st))) return rc;
+    std::vector<double> bn2(nrhs), rn2(nrhs);
+    {  // ||b||^2
+      k_residual<<<dim3(nblk_r, nrhs), RED_THREADS, 0, st>>>(nreal, b, b, b, -1.0, nullptr, bpart.as<double>()); note_launch();
+      // b - b - (-1) b = b
+      k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
+      BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+      BRI_CUDA(cudaStreamSynchronize(st));
+    }
+    const int max_rounds = 8;
+    for (int round = 0; round < max_rounds; ++round) {
+      // FP64 residuals of every (shift, rhs); collect the unconverged ones
+      std::vector<int> todo_k, todo_s;
+      std::vector<double> todo_sig;
+      if ((rc = bres.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
+      double worst = 0.0;
+      for (int k = 0; k < n; ++k) {
+        rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k],
+                        bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(), btmp2.as<double>(),
+                        bpart.as<double>(), bdsum.as<double>(), rn2.data(), &cnt);
+        if (rc) return rc;
+        for (int s = 0; s < nrhs; ++s) {
+          double rel = std::sqrt(rn2[s] / std::max(bn2[s], 1e-300));
+          worst = std::max(worst, rel);
+          if (rel > tol) {
+            todo_k.push_back(k);
+            todo_s.push_back(s);
+            todo_sig.push_back(sig[k]);
+          }
+        }
+      }
+      if (todo_k.empty()) break;
+      refinements++;
+      // batched FP32 correction solves, one system per unconverged (shift, rhs)
+      const int ns = (int)todo_k.size();
+      const int chunk = 32;
+      for (int c0i = 0; c0i < ns; c0i += chunk) {
+        const int m = std::min(chunk, ns - c0i);
+        DevBuf brhs, bsol;
+        if ((rc = brhs.alloc(sizeof(float) * nreal * m, st))) return rc;
+        if ((rc = bsol.alloc(sizeof(float) * nreal * m, st))) return rc;
+        for (int j = 0; j < m; ++j) {
+          const int k = todo_k[c0i + j], s = todo_s[c0i + j];
+          k_convert<double, float><<<512, 256, 0, st>>>(
+              nreal, bres.as<double>() + ((int64_t)k * nrhs + s) * nreal, brhs.as<float>() + (int64_t)j * nreal); note_launch();
+        }
+        int itc = 0;
+        rc = multishift_solve<float>(c, prec, m0, m, 1, todo_sig.data() + c0i, brhs.as<float>(), bsol.as<float>(),
+                                     1e-5, maxiter, &itc, &cnt);
+        if (rc < 0) return rc;
+        for (int j = 0; j < m; ++j) {
+          const int k = todo_k[c0i + j], s = todo_s[c0i + j];
+          k_accumulate<<<512, 256, 0, st>>>(nreal, X + ((int64_t)k * nrhs + s) * nreal,
+                                            bsol.as<float>() + (int64_t)j * nreal); note_launch();
+        }
+        BRI_LAUNCH_CHECK("refinement accumulate");
+      }
+      if (round == max_rounds - 1) solve_rc = BRI_NOT_CONVERGED;
+    }
+  } else {
+    set_error("sign_apply_multishift: unknown precision");
+    return BRI_ERR_INVALID;
+  }
+
+  // optional FP64 true residuals for the statistics
+  if (stats && stats->want_true_residual) {
+    DevBuf btmp1, btmp2, bpart, bdsum;
+    const int nblk_r = grid_for(nreal / 2, nrhs);
+    if ((rc = btmp1.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+    if ((rc = btmp2.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+    if ((rc = bpart.alloc(sizeof(double) * nblk_r * nrhs, st))) return rc;
+    if ((rc = bdsum.alloc(sizeof(double) * nrhs, st))) return rc;
+    std::vector<double> bn2(nrhs), rn2(nrhs);
+    k_residual<<<dim3(nblk_r, nrhs), RED_THREADS, 0, st>>>(nreal, b, b, b, -1.0, nullptr, bpart.as<double>()); note_launch();
+    k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
+    BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    BRI_CUDA(cudaStreamSynchronize(st));
+    Counters dummy;
+    stats->max_true_residual = 0.0;
+    for (int k = 0; k < n; ++k) {
+      rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k], nullptr, btmp1.as<double>(),
+                      btmp2.as<double>(), bpart.as<double>(), bdsum.as<double>(), rn2.data(), &dummy);
+      if (rc) return rc;
+      double worst = 0.0;
+      for (int s = 0; s < nrhs; ++s) worst = std::max(worst, std::sqrt(rn2[s] / std::max(bn2[s], 1e-300)));
+      if (k < NS) stats->shift_residual[k] = worst;
+      stats->max_true_residual = std::max(stats->max_true_residual, worst);
+    }
+  }
+
+  // y = b_coeff b + out_scale D (c0 b + sum_i w_i X_i)
+  DevBuf bacc, bz, bw;
+  if ((rc = bacc.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  if ((rc = bz.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  if ((rc = bw.alloc(sizeof(double) * NS, st))) return rc;
+  BRI_CUDA(cudaMemcpyAsync(bw.as<double>(), w, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  k_rational<<<dim3(grid_for(nreal, nrhs), nrhs), RED_THREADS, 0, st>>>(nreal, nrhs, n, c0, bw.as<double>(), b, X,
+                                                                       bacc.as<double>()); note_launch();
+  BRI_LAUNCH_CHECK("k_rational");
+  if ((rc = dirac_bri(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) return rc;
+  cnt.matvecs += 1;
+  cnt.matvecs64 += 1;
+  k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), (double*)y); note_launch();
+  BRI_LAUNCH_CHECK("k_axpby");
+  BRI_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->iterations = iters;
+    stats->matvecs = cnt.matvecs;
+    stats->matvecs_f64 = cnt.matvecs64;
+    stats->refinements = refinements;
+    stats->n_shifts = n;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return solve_rc;
+}
+
+}  // namespace bri

@@ -62,18 +62,43 @@ _LAMBDA = _gell_mann()
 
 
 def su3_exp_i(h):
-    """exp(i h) for a stack of Hermitian 3x3 matrices h (via eigh)."""
+    """exp(i h) for a stack of Hermitian 3x3 matrices h (numpy or torch, via eigh)."""
+    if _is_torch(h):
+        import torch
+        flat = h.reshape(-1, 3, 3)
+        out = torch.empty_like(flat)
+        chunk = 1 << 16  # bounded batched-eigh workspace
+        for i in range(0, flat.shape[0], chunk):
+            ev, vec = torch.linalg.eigh(flat[i:i + chunk])
+            ph = torch.exp(1j * ev.to(h.dtype))
+            out[i:i + chunk] = (vec * ph.unsqueeze(-2)) @ vec.conj().transpose(-1, -2)
+        return out.reshape(h.shape)
     ev, vec = np.linalg.eigh(h)
     return np.einsum("...ab,...b,...cb->...ac", vec, np.exp(1j * ev), vec.conj())
 
 
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
 def _shift(f, mu, s):
     """Field value at n + s*e_mu (periodic); f has leading axes (t, z, y, x)."""
+    if _is_torch(f):
+        import torch
+        return torch.roll(f, -s, dims=3 - mu)
     return np.roll(f, -s, axis=3 - mu)
 
 
 def _dag(m):
+    if _is_torch(m):
+        return m.transpose(-1, -2).conj()
     return np.swapaxes(m, -1, -2).conj()
+
+
+def _trace(m):
+    if _is_torch(m):
+        return m.diagonal(dim1=-2, dim2=-1).sum(-1)
+    return np.trace(m, axis1=-2, axis2=-1)
 
 
 def plaquette(u):
@@ -83,15 +108,15 @@ def plaquette(u):
         for nu in range(mu + 1, 4):
             um, un = u[..., mu, :, :], u[..., nu, :, :]
             p = um @ _shift(un, mu, 1) @ _dag(_shift(um, nu, 1)) @ _dag(un)
-            tot += np.trace(p, axis1=-2, axis2=-1).real.mean() / 3.0
+            tot += float(_trace(p).real.mean()) / 3.0
     return tot / 6.0
 
 
 def stout_smear(u, rho, steps):
     """Isotropic stout smearing, ``steps`` sweeps with parameter ``rho``."""
-    u = u.copy()
+    u = u.clone() if _is_torch(u) else u.copy()
     for _ in range(int(steps)):
-        c = np.zeros_like(u)
+        c = u * 0
         for mu in range(4):
             um = u[..., mu, :, :]
             for nu in range(4):
@@ -100,20 +125,31 @@ def stout_smear(u, rho, steps):
                 un = u[..., nu, :, :]
                 up = un @ _shift(um, nu, 1) @ _dag(_shift(un, mu, 1))
                 un_m = _shift(un, nu, -1)
-                dn = _dag(un_m) @ _shift(um, nu, -1) @ _shift(_shift(un, nu, -1), mu, 1)
+                dn = _dag(un_m) @ _shift(um, nu, -1) @ _shift(un_m, mu, 1)
                 c[..., mu, :, :] += up + dn
-        c *= rho
+        c = c * rho
         om = c @ _dag(u)
         a = _dag(om) - om
-        tr = np.trace(a, axis1=-2, axis2=-1)[..., None, None]
-        q = 0.5j * a - (1j / 6.0) * tr * np.eye(3)
+        tr = _trace(a)[..., None, None]
+        if _is_torch(u):
+            import torch
+            eye = torch.eye(3, dtype=u.dtype, device=u.device)
+        else:
+            eye = np.eye(3)
+        q = 0.5j * a - (1j / 6.0) * tr * eye
         q = 0.5 * (q + _dag(q))  # remove rounding-level anti-Hermitian part
         u = su3_exp_i(q) @ u
     return u
 
 
-def _raw_field(shape, eps, rng):
+def _raw_field(shape, eps, rng, device=None):
     omega = rng.standard_normal(shape + (4, 8))
+    if device is not None:
+        import torch
+        om = torch.from_numpy(omega).to(device)
+        lam = torch.from_numpy(_LAMBDA).to(device)
+        q = torch.einsum("...a,aij->...ij", om.to(torch.complex128), lam) * 0.5
+        return su3_exp_i(eps * q)
     q = np.einsum("...a,aij->...ij", omega, _LAMBDA) * 0.5
     return su3_exp_i(eps * q)
 
@@ -145,18 +181,23 @@ def tuned_eps(smear_rho=0.0, smear_steps=0, target=TARGET_PLAQUETTE):
     return 0.5 * (lo + hi)
 
 
-def gauge_field(dims, seed, smear_rho=0.0, smear_steps=0, eps=None):
-    """Seeded SU(3) field U[t,z,y,x,mu,3,3] (complex128), plaquette ~ 0.6.
+def gauge_field(dims, seed, smear_rho=0.0, smear_steps=0, eps=None, device=None):
+    """Seeded SU(3) field U[t,z,y,x,mu,3,3] (complex128 numpy), plaquette ~ 0.6.
 
-    ``eps=0`` gives the free field U = 1.
+    ``eps=0`` gives the free field U = 1.  ``device`` (e.g. "cuda") runs the
+    matrix exponentials and smearing with torch on that device, for large
+    volumes; the random numbers are the same numpy PCG64 stream either way,
+    and the returned array is what both the oracle and the CUDA path consume.
     """
     shape = lattice_shape(dims)
     if eps is None:
         eps = tuned_eps(float(smear_rho), int(smear_steps))
     rng = np.random.Generator(np.random.PCG64(seed))
-    u = _raw_field(shape, eps, rng)
+    u = _raw_field(shape, eps, rng, device)
     if smear_steps:
         u = stout_smear(u, smear_rho, smear_steps)
+    if device is not None:
+        u = u.cpu().numpy()
     return np.ascontiguousarray(u)
 
 

@@ -1,0 +1,186 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several 128-site thread blocks with a ragged tail; the smallest
+lattice 2^4 makes every neighbour wrap.  Tolerances: FP64 1e-12 relative
+(max-norm), a single FP32 matvec 1e-5, BF16-stored links 1e-2 (8-bit
+mantissa: each link element carries a relative rounding error up to 2^-9,
+and the 80 hop terms add with random signs), solver results 1e-10.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic_fields as sf
+from oracle import dirac, kl, links, overlap
+from paper_1701_00726_gb300 import PREC_F32, PREC_F32_BF16, PREC_F64, BriError, Lattice, kl_coeffs
+
+pytestmark = pytest.mark.gpu
+
+RAGGED = (6, 5, 4, 3)  # 360 sites: two full 128-site blocks and a ragged tail
+
+
+def relerr(got, want):
+    return float(np.abs(got - want).max() / max(np.abs(want).max(), 1e-300))
+
+
+def _lattice(dims, u, c_sw=0.0, anti=False):
+    lat = Lattice(dims, antiperiodic_t=anti)
+    lat.build_links(torch.from_numpy(u).cuda().contiguous(), c_sw)
+    return lat
+
+
+def test_kl_coeffs_abi():
+    for kind in (0, 1):
+        for n in (1, 2, 5, 8, 12, 16, 32):
+            for s in (1.0, 2.5):
+                c0, w, sig = kl_coeffs(n, kind, s)
+                oc0, ow, osig = kl.kl_coeffs(n, kind, s)
+                assert abs(c0 - oc0) <= 1e-15 * max(1.0, abs(oc0))
+                np.testing.assert_allclose(w, ow, rtol=2e-15)
+                np.testing.assert_allclose(sig, osig, rtol=2e-15)
+    with pytest.raises(BriError):
+        kl_coeffs(0)
+    with pytest.raises(BriError):
+        kl_coeffs(33)
+
+
+@pytest.mark.parametrize("anti", [False, True])
+def test_links_vs_path_enumeration(anti):
+    dims = (3, 4, 2, 3)
+    u = sf.gauge_field(dims, 7)
+    lat = _lattice(dims, u, anti=anti)
+    got = lat.links().cpu().numpy()
+    want = links.stored_links(links.offaxis_links(u, anti))
+    assert np.abs(got - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("dims", [RAGGED, (2, 2, 2, 2)])
+@pytest.mark.parametrize("c_sw", [0.0, 1.0])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_bri_apply_f64(dims, c_sw, dagger):
+    u = sf.gauge_field(dims, 3)
+    x = sf.gaussian_source(dims, 3, 1003)
+    m0 = -1.0
+    lat = _lattice(dims, u, c_sw)
+    y = lat.bri_apply(torch.from_numpy(x).cuda(), m0, dagger=dagger).cpu().numpy()
+    op = dirac.DiracOperator(u, "bri", m0=m0, c_sw=c_sw)
+    want = op.apply_dagger(x) if dagger else op.apply(x)
+    assert relerr(y, want) < 1e-12
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_bri_apply_f32(bf16, dagger):
+    dims = RAGGED
+    u = sf.gauge_field(dims, 4)
+    x = sf.gaussian_source(dims, 2, 1004)
+    lat = _lattice(dims, u, 1.0)
+    y = lat.bri_apply(torch.from_numpy(x).to(torch.complex64).cuda(), -1.0, dagger=dagger,
+                      bf16_links=bf16).cpu().numpy()
+    op = dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0)
+    want = op.apply_dagger(x) if dagger else op.apply(x)
+    assert relerr(y, want) < (1e-2 if bf16 else 1e-5)
+
+
+@pytest.mark.parametrize("c_sw", [0.0, 1.0])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("anti", [False, True])
+def test_wils_apply(c_sw, dagger, anti):
+    dims = RAGGED
+    u = sf.gauge_field(dims, 5)
+    x = sf.gaussian_source(dims, 2, 1005)
+    lat = _lattice(dims, u, c_sw, anti)
+    op = dirac.DiracOperator(u, "wil", m0=-0.7, c_sw=c_sw, antiperiodic_t=anti)
+    want = op.apply_dagger(x) if dagger else op.apply(x)
+    y64 = lat.wils_apply(torch.from_numpy(x).cuda(), -0.7, dagger=dagger).cpu().numpy()
+    assert relerr(y64, want) < 1e-12
+    y32 = lat.wils_apply(torch.from_numpy(x).to(torch.complex64).cuda(), -0.7, dagger=dagger).cpu().numpy()
+    assert relerr(y32, want) < 1e-5
+
+
+def test_antiperiodic_bri():
+    dims = RAGGED
+    u = sf.gauge_field(dims, 6)
+    x = sf.gaussian_source(dims, 1, 1006)
+    lat = _lattice(dims, u, 1.0, anti=True)
+    y = lat.bri_apply(torch.from_numpy(x).cuda(), -1.0).cpu().numpy()
+    want = dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0, antiperiodic_t=True).apply(x)
+    assert relerr(y, want) < 1e-12
+
+
+def test_invalid_arguments():
+    dims = (4, 4, 4, 4)
+    u = sf.gauge_field(dims, 0)
+    lat = Lattice(dims)
+    x = torch.zeros((1,) + sf.lattice_shape(dims) + (4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(BriError):  # links not built yet
+        lat.bri_apply(x, -1.0)
+    lat.build_links(torch.from_numpy(u).cuda(), 0.0)
+    with pytest.raises(BriError):  # wrong size
+        lat.bri_apply(x[..., :2], -1.0)
+    with pytest.raises(BriError):
+        lat.overlap_apply(x, n=0)
+    with pytest.raises(BriError):
+        lat.overlap_apply(x, n=8, rho=2.5)
+    with pytest.raises(BriError):
+        Lattice((1, 4, 4, 4))
+
+
+@pytest.mark.parametrize("prec,tol,bound", [(PREC_F64, 1e-13, 1e-12), (PREC_F32, 1e-11, 1e-10),
+                                            (PREC_F32_BF16, 1e-11, 1e-10)])
+def test_overlap_c1_workload(prec, tol, bound):
+    """4^4, c_SW = 0, rho = 1, KL order 8, 12 Gaussian sources (FP64, mixed FP32, mixed BF16 links)."""
+    dims = (4, 4, 4, 4)
+    u = sf.gauge_field(dims, 0)
+    x = sf.gaussian_source(dims, 12, 1000)
+    lat = _lattice(dims, u)
+    y, st = lat.overlap_apply(torch.from_numpy(x).cuda(), n=8, rho=1.0, tol=tol, prec=prec, want_true_residual=True)
+    assert st["converged"]
+    assert st["max_true_residual"] < 10 * tol
+    want, _ = overlap.overlap_apply(dirac.DiracOperator(u, "bri", m0=-1.0), x, 1.0, 8, 1e-13)
+    assert relerr(y.cpu().numpy(), want) < bound
+
+
+def test_overlap_clover_massive_and_sign():
+    dims = RAGGED
+    u = sf.gauge_field(dims, 8)
+    x = sf.gaussian_source(dims, 2, 1008)
+    lat = _lattice(dims, u, 1.0)
+    kern = dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0)
+    xt = torch.from_numpy(x).cuda()
+    y, st = lat.overlap_apply(xt, n=6, rho=1.0, am=0.1, tol=1e-13)
+    want, _ = overlap.overlap_apply(kern, x, 1.0, 6, 1e-13, am=0.1)
+    assert relerr(y.cpu().numpy(), want) < 1e-12
+    s, _ = lat.sign_apply(xt, n=6, rho=1.0, tol=1e-13)
+    swant, _ = overlap.sign_apply(kern, x, 6, 1e-13)
+    assert relerr(s.cpu().numpy(), swant) < 1e-12
+    # upper-diagonal family g_{2n} (Tab. 6)
+    s1, _ = lat.sign_apply(xt, n=3, rho=1.0, tol=1e-13, kind=1)
+    swant1, _ = overlap.sign_apply(kern, x, 3, 1e-13, kind=1)
+    assert relerr(s1.cpu().numpy(), swant1) < 1e-12
+
+
+def test_bri_apply_full_size_sampled():
+    """24^3 x 48 (the benchmark lattice), FP32 spinors / FP32 and BF16 links, 12 sources:
+    sampled sites against the per-site oracle, and gamma5-hermiticity of the FP64 path."""
+    dims = (24, 24, 24, 48)
+    u = sf.gauge_field(dims, 1, 0.1, 3, device="cuda")
+    x = sf.gaussian_source(dims, 12, 1001)
+    lat = _lattice(dims, u, 1.0)
+    xt = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(0)
+    sites = [tuple(int(rng.integers(0, L)) for L in dims) for _ in range(12)]
+    sites += [(0, 0, 0, 0), (23, 23, 23, 47), (0, 23, 0, 47)]
+    want = dirac.apply_at_sites(u, "bri", -1.0, 1.0, x, sites)
+    for bf16, bound in ((False, 1e-5), (True, 1e-2)):
+        y = lat.bri_apply(xt.to(torch.complex64), -1.0, bf16_links=bf16)
+        got = np.stack([y[:, st, sz, sy, sx].cpu().numpy() for (sx, sy, sz, st) in sites], axis=1)
+        assert relerr(got, want) < bound
+    y64 = lat.bri_apply(xt[:2], -1.0)
+    got = np.stack([y64[:, st, sz, sy, sx].cpu().numpy() for (sx, sy, sz, st) in sites], axis=1)
+    assert relerr(got, want[:2]) < 1e-12
+    # <phi, D psi> = <D^dagger phi, psi>
+    phi, psi = xt[0:1], xt[1:2]
+    lhs = torch.vdot(phi.flatten(), lat.bri_apply(psi, -1.0).flatten())
+    rhs = torch.vdot(lat.bri_apply(phi, -1.0, dagger=True).flatten(), psi.flatten())
+    assert abs((lhs - rhs).item()) < 1e-11 * abs(lhs.item())
