@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the Brillouin-kernel overlap hot path on GB300.
+
+One step = one application of the massless overlap operator
+D_ov = rho (1 + gamma5 f_16,16(H)), H = gamma5 D_bri(-rho), to a batch of
+right-hand sides on a 24^3 x 48 lattice: multi-shift CG on D^dagger D + sigma_i
+(Kenney-Laub order 16) in FP32 with FP64 reductions and FP64 defect-correction
+refinement of every shift to a true relative residual of 1e-10, then one FP64
+application of D.  Inputs (stout-smeared synthetic SU(3) field, complex
+Gaussian sources) are resident in HBM when the timed region starts.
+
+Printed (rank 0, one JSON line): D_ov applies per second over all ranks, the
+stencil's roofline figures measured with CUDA events inside the timed region,
+an end-to-end figure through the same C ABI call with host buffers, and the
+FP64 CPU oracle timed on a bounded sample.  ``--impl reference`` times the
+oracle alone.
+
+Multi-GPU (torchrun): every rank runs an independent replica (own gauge field
+and sources), there is no data-path collective; the per-step time is the
+maximum over ranks and the value counts the applications of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D_ov applies/s at 24^3x48 (mixed vs FP64, 1e-10); bri_apply HBM GB/s vs roofline"
+UNIT = "D_ov applies/s"
+DIMS = (24, 24, 24, 48)
+KL_ORDER = 16
+RHO = 1.0
+C_SW = 1.0
+TOL = 1e-10
+GAUGE_SEED = 1
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes of one FP32 Brillouin stencil launch: per site the 40
+# stored links (40 x 72 B) and the clover blocks (72 floats) once, and per site
+# and right-hand side one spinor read and one written (2 x 96 B) (App. C)
+LINK_BYTES = {1: 40 * 72, 2: 40 * 36}
+CLOVER_BYTES = 72 * 4
+SPINOR_BYTES = 2 * 96
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=12)
+    ap.add_argument("--links", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-compare", action="store_true",
+                    help="also time one plain FP64 D_ov (1 rhs) outside the timed region")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    v = d[k]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def stencil_traffic():
+    """dram bytes per launch of the FP32 stencil from the committed ncu summary,
+    valid only while the stencil source is unchanged (hash match)."""
+    src = os.path.join(ROOT, "paper_1701_00726_gb300", "csrc", "dirac.cu")
+    p = os.path.join(ROOT, "profiles", "bri_stencil_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("dirac_cu_sha256_16") != h:
+            return None
+        return d
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.out = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.out)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_sample(dims, n, tol, nrhs=1):
+    """Time the FP64 oracle's D_ov on a small lattice (same generator, same
+    solver settings); returns (seconds, site count)."""
+    import synthetic_fields as sf
+    from oracle import dirac, overlap
+    u = sf.gauge_field(dims, GAUGE_SEED, 0.1, 3)
+    x = sf.gaussian_source(dims, nrhs, GAUGE_SEED + 1000)
+    t0 = time.perf_counter()
+    kern = dirac.DiracOperator(u, "bri", m0=-RHO, c_sw=C_SW)
+    overlap.overlap_apply(kern, x, RHO, n, tol)
+    return time.perf_counter() - t0, dims[0] * dims[1] * dims[2] * dims[3] * nrhs
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sample = (4, 4, 4, 4)
+    vfull = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
+    for _ in range(args.warmup):
+        oracle_sample(sample, KL_ORDER, TOL)
+    t = 0.0
+    for _ in range(args.steps):
+        dt, vs = oracle_sample(sample, KL_ORDER, TOL)
+        t += dt * vfull / vs  # seconds one full-volume application would take
+    value = args.steps / t
+    desc = (f"FP64 numpy oracle: one D_ov (KL order {KL_ORDER}, tol {TOL:g}, c_SW {C_SW:g}) per step on a 4^4 "
+            f"lattice, time scaled by volume to 24^3x48")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "24^3x48 overlap apply (oracle, volume-scaled sample)", "kl_order": KL_ORDER,
+                   "tol": TOL, "rho": RHO, "c_sw": C_SW},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import synthetic_fields as sf
+    from paper_1701_00726_gb300 import PREC_F32, PREC_F32_BF16, PREC_F64, Lattice
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = PREC_F32_BF16 if args.links == "bf16" else PREC_F32
+    nrhs = args.nrhs
+    vol = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
+
+    u = sf.gauge_field(DIMS, GAUGE_SEED + rank, 0.1, 3, device="cuda")
+    x_host = sf.gaussian_source(DIMS, nrhs, GAUGE_SEED + 1000 + rank)
+    lat = Lattice(DIMS)
+    lat.build_links(torch.from_numpy(u).cuda(), C_SW)
+    del u
+    x = torch.from_numpy(x_host).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    stats = []
+    for _ in range(args.warmup):
+        _, st = lat.overlap_apply(x, n=KL_ORDER, rho=RHO, tol=TOL, prec=prec, out=y)
+    barrier()
+    lat.profile(True)
+    lat.profile_read(0, prec)
+    launches0 = Lattice.kernel_launches()
+    clocks = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, st = lat.overlap_apply(x, n=KL_ORDER, rho=RHO, tol=TOL, prec=prec, out=y)
+        stats.append(st)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = Lattice.kernel_launches() - launches0
+    nlaunch, kms, units = lat.profile_read(0, prec)
+    lat.profile(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    applies = args.steps * nrhs * world
+    value = applies / elapsed
+
+    # roofline of the dominant kernel (the FP32 Brillouin stencil)
+    peak, peak_src = measured_peak()
+    alg_bytes = nlaunch * vol * (LINK_BYTES[prec] + CLOVER_BYTES) + units * SPINOR_BYTES
+    achieved = alg_bytes / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    traffic = stencil_traffic()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_src,
+            "kernel": "bri_mrhs_kernel<float," + ("bf16x2" if prec == PREC_F32_BF16 else "float2") + ",NR>",
+            "launches": nlaunch, "avg_launch_ms": round(kms / max(nlaunch, 1), 4),
+            "alg_bytes_per_launch": int(alg_bytes / max(nlaunch, 1)),
+            "stencil_share_of_step": round((kms / 1e3) / elapsed, 4) if world == 1 else None,
+            "traffic": None if traffic is None else traffic.get("dram_bytes_per_launch")}
+
+    # end to end through the same C ABI call with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xd = xh.to("cuda", non_blocking=True)
+            yd, _ = lat.overlap_apply(xd, n=KL_ORDER, rho=RHO, tol=TOL, prec=prec)
+            yh.copy_(yd, non_blocking=True)
+            torch.cuda.synchronize()
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": applies / te, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 16),
+               "d2h_bytes_per_step": int(yh.numel() * 16)}
+
+    fp64 = None
+    if args.fp64_compare and rank == 0:
+        xs = x[:1].contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st64 = lat.overlap_apply(xs, n=KL_ORDER, rho=RHO, tol=TOL, prec=PREC_F64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        fp64 = {"applies_per_s_1rhs": 1.0 / t64, "seconds": t64, "iterations": st64["iterations"],
+                "mixed_over_fp64": value / world / (1.0 / t64)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = (4, 4, 4, 4)
+        dt, vs = oracle_sample(sample, KL_ORDER, TOL)
+        cpu = {"value": 1.0 / (dt * vol / vs), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 numpy-oracle D_ov on 4^4 (same generator, KL order {KL_ORDER}, tol {TOL:g}, "
+                         f"c_SW {C_SW:g}, 1 rhs), {dt:.1f} s, scaled by volume to 24^3x48"}
+
+    if rank == 0:
+        last = stats[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"24^3x48 massless overlap apply, {nrhs} rhs per step, stout 3x0.1, c_SW=1, "
+                                   f"rho=1, KL order {KL_ORDER}, final true residual {TOL:g} per shift",
+                       "lattice": list(DIMS), "nrhs": nrhs, "kl_order": KL_ORDER, "tol": TOL,
+                       "inner": "fp32 spinors, " + ("bf16" if prec == PREC_F32_BF16 else "fp32") +
+                                " links, fp64 reductions, fp64 refinement",
+                       "l2": "inputs larger than L2 (links 1.9 GB FP32)", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "solver": {"iterations": last["iterations"], "matvecs": last["matvecs"],
+                       "matvecs_f64": last["matvecs_f64"], "refinements": last["refinements"],
+                       "phase_seconds": [round(v, 4) for v in last["phase_seconds"]]},
+        }
+        if fp64 is not None:
+            line["fp64_gpu"] = fp64
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

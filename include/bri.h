@@ -79,6 +79,7 @@ typedef struct bri_stats {
   int want_true_residual;  /* input: compute FP64 true residuals per shift */
   int maxiter;             /* input: iteration cap (0 = default 20000) */
   double seconds;          /* wall time of the call */
+  double phase_seconds[4]; /* main multi-shift solve, FP64 residuals, corrections, final D */
 } bri_stats;
 
 /* Create a context for one lattice.  dims: {Lx,Ly,Lz,Lt}, each >= 2.

@@ -50,8 +50,10 @@ def multishift_cg(apply_a, b, sigmas, tol, maxiter=100000):
     for it in range(1, maxiter + 1):
         q = apply_a(p[0]) + base * p[0]
         alpha = rr / vdot(p[0], q).real
-        zeta_next = np.empty(n)
+        zeta_next = zeta.copy()  # frozen shifts keep their last value
         for i in range(n):
+            if not active[i]:
+                continue
             den = (alpha * beta_prev * (zeta_prev[i] - zeta[i])
                    + zeta_prev[i] * alpha_prev * (1.0 + delta[i] * alpha))
             zeta_next[i] = zeta[i] * zeta_prev[i] * alpha_prev / den

@@ -37,6 +37,7 @@ class BriStats(ctypes.Structure):
         ("want_true_residual", ctypes.c_int),
         ("maxiter", ctypes.c_int),
         ("seconds", ctypes.c_double),
+        ("phase_seconds", ctypes.c_double * 4),
     ]
 
     def as_dict(self):
@@ -45,6 +46,7 @@ class BriStats(ctypes.Structure):
             "refinements": self.refinements, "n_shifts": self.n_shifts,
             "max_true_residual": self.max_true_residual,
             "shift_residual": list(self.shift_residual)[: self.n_shifts], "seconds": self.seconds,
+            "phase_seconds": list(self.phase_seconds),
         }
 
 

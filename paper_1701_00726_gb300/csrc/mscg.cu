@@ -16,12 +16,16 @@
 // block partials summed in a fixed order (deterministic).
 //
 // Mixed precision (prec = F32 or F32/BF16 links): the multi-shift solve runs
-// with FP32 vectors and operator (FP64 scalars and reductions) to ~1e-6, then
-// each shift is refined by defect correction: the FP64 residual
-// r_i = b - (A + sigma_i) X_i is computed with the FP64 operator and an FP32 CG
-// correction (A + sigma_i) e_i = r_i is added in FP64, until every shift has
-// ||r_i|| <= tol ||b||.  All corrections of one round run as one batched CG
-// with a per-system shift.
+// with FP32 vectors and operator (FP64 scalars and reductions) to ~1e-6 (BF16
+// links: only this phase uses them).  Then every shift is refined by defect
+// correction: its FP64 residual r_i = b - (A + sigma_i) X_i is computed once
+// with the FP64 operator, an FP32 CG correction (A + sigma_i) e_i = r_i is
+// added to X_i in FP64, and r_i is updated with the FP32 operator applied to
+// e_i.  The update's rounding error (~eps32 kappa_i ||r_i||, kappa_i estimated
+// from the Lanczos coefficients of the first phase) is accumulated per shift;
+// where it could matter the residual is recomputed in FP64 before the shift is
+// declared converged.  All corrections of a round run as one batched CG with a
+// per-system shift, hardest systems first, and converged systems drop out.
 #include "internal.cuh"
 #include "cplx.cuh"
 
@@ -38,6 +42,7 @@ constexpr int RED_THREADS = 256;
 
 struct MsState {
   double rr, bnorm2, pq, alpha, alpha_prev, beta_prev, tol2;
+  double lam_max;  // largest diagonal entry of the CG Lanczos matrix (estimate of lambda_max(A + sigma_base))
   double sig_base;
   double delta[NS];
   double zeta[NS], zeta_prev[NS], zeta_next[NS];
@@ -111,11 +116,16 @@ __global__ void k_shift_dot(int64_t n2, const MsState* __restrict__ st, const ty
   if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
 }
 
-// x_i += alpha_i p_i (active i); r -= alpha q; partial ||r||^2
+// One pass over the shifted vectors per iteration.  For every active shift
+// i > 0 the direction update left over from the previous iteration,
+// p_i = zeta_i r + beta_i p_i, is applied first (r is still the previous
+// residual here), then x_i += alpha_i p_i; finally r -= alpha q and the
+// partial ||r||^2.  The base direction p_0 is updated separately (k_update_p0)
+// because the next matrix-vector product needs it.
 template <typename R>
-__global__ void k_update_xr(int64_t n2, int nsys, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ q,
-                            typename P2<R>::T* r, const typename P2<R>::T* __restrict__ p, typename P2<R>::T* x,
-                            double* part) {
+__global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__ st,
+                               const typename P2<R>::T* __restrict__ q, typename P2<R>::T* r, typename P2<R>::T* p,
+                               typename P2<R>::T* x, double* part, int first) {
   using T = typename P2<R>::T;
   const int s = blockIdx.y;
   if (st[s].done) return;
@@ -123,16 +133,24 @@ __global__ void k_update_xr(int64_t n2, int nsys, const MsState* __restrict__ st
   const R alpha = (R)st[s].alpha;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    T rv = r[s * n2 + i];
     for (int k = 0; k < nshift; ++k) {
       if (!st[s].active[k]) continue;
-      const R a = (R)st[s].a_s[k];
       const int64_t o = ((int64_t)k * nsys + s) * n2 + i;
-      T pv = p[o], xv = x[o];
+      T pv = p[o];
+      if (k > 0 && !first) {
+        const R z = (R)st[s].zeta[k], bt = (R)st[s].b_s[k];
+        pv.x = fma(bt, pv.x, z * rv.x);
+        pv.y = fma(bt, pv.y, z * rv.y);
+        p[o] = pv;
+      }
+      const R a = (R)st[s].a_s[k];
+      T xv = x[o];
       xv.x = fma(a, pv.x, xv.x);
       xv.y = fma(a, pv.y, xv.y);
       x[o] = xv;
     }
-    T rv = r[s * n2 + i], qv = q[s * n2 + i];
+    const T qv = q[s * n2 + i];
     rv.x = fma(-alpha, qv.x, rv.x);
     rv.y = fma(-alpha, qv.y, rv.y);
     r[s * n2 + i] = rv;
@@ -142,24 +160,20 @@ __global__ void k_update_xr(int64_t n2, int nsys, const MsState* __restrict__ st
   if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
 }
 
-// p_i = zeta_i r + beta_i p_i (active i)
+// p_0 = r + beta p_0 (base direction, zeta_0 = 1)
 template <typename R>
-__global__ void k_update_p(int64_t n2, int nsys, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ r,
-                           typename P2<R>::T* p) {
+__global__ void k_update_p0(int64_t n2, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ r,
+                            typename P2<R>::T* p) {
   using T = typename P2<R>::T;
   const int s = blockIdx.y;
-  const int nshift = st[s].nshift;
+  if (st[s].done) return;
+  const R bt = (R)st[s].b_s[0];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-    T rv = r[s * n2 + i];
-    for (int k = 0; k < nshift; ++k) {
-      if (!st[s].active[k]) continue;
-      const R z = (R)st[s].zeta[k], bt = (R)st[s].b_s[k];
-      const int64_t o = ((int64_t)k * nsys + s) * n2 + i;
-      T pv = p[o];
-      pv.x = fma(bt, pv.x, z * rv.x);
-      pv.y = fma(bt, pv.y, z * rv.y);
-      p[o] = pv;
-    }
+    const T rv = r[s * n2 + i];
+    T pv = p[s * n2 + i];
+    pv.x = fma(bt, pv.x, rv.x);
+    pv.y = fma(bt, pv.y, rv.y);
+    p[s * n2 + i] = pv;
   }
 }
 
@@ -172,6 +186,7 @@ __global__ void k_scalar_init(MsState* st, const double* part, int nblk) {
   if (threadIdx.x == 0) {
     MsState& S = st[s];
     S.rr = t;
+    S.lam_max = 0.0;
     S.bnorm2 = t;
     S.alpha_prev = 1.0;
     S.beta_prev = 0.0;
@@ -205,7 +220,11 @@ __global__ void k_scalar_alpha(MsState* st, const double* part, int nblk) {
     const double alpha = S.rr / pq;
     S.pq = pq;
     S.alpha = alpha;
+    // Lanczos diagonal T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}
+    const double tkk = 1.0 / alpha + (S.iters > 0 ? S.beta_prev / S.alpha_prev : 0.0);
+    S.lam_max = fmax(S.lam_max, tkk);
     for (int k = 0; k < S.nshift; ++k) {
+      if (!S.active[k]) continue;  // frozen shifts keep their last coefficients
       const double den = alpha * S.beta_prev * (S.zeta_prev[k] - S.zeta[k]) +
                          S.zeta_prev[k] * S.alpha_prev * (1.0 + S.delta[k] * alpha);
       const double zn = S.zeta[k] * S.zeta_prev[k] * S.alpha_prev / den;
@@ -231,6 +250,7 @@ __global__ void k_scalar_beta(MsState* st, const double* part, int nblk) {
     }
     const double beta = rr / S.rr;
     for (int k = 0; k < S.nshift; ++k) {
+      if (!S.active[k]) continue;
       const double ratio = S.zeta_next[k] / S.zeta[k];
       S.b_s[k] = beta * ratio * ratio;
       S.zeta_prev[k] = S.zeta[k];
@@ -247,6 +267,39 @@ __global__ void k_scalar_beta(MsState* st, const double* part, int nblk) {
       S.done = 1;
     }
   }
+}
+
+// rhs32[j] = (float) res[slot[j]]
+__global__ void k_gather_f32(int64_t n, const double* __restrict__ res, const long long* __restrict__ slot,
+                             float* out) {
+  const int j = blockIdx.y;
+  const double* src = res + slot[j] * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[j * n + i] = (float)src[i];
+}
+
+// X[slot] += e ; res[slot] -= (A e + sigma e) ; partial ||res||^2
+__global__ void k_correct(int64_t n, const long long* __restrict__ slot, const double* __restrict__ sig,
+                          const float* __restrict__ e, const float* __restrict__ ae, double* X, double* res,
+                          double* part) {
+  const int j = blockIdx.y;
+  const double sg = sig[j];
+  double* xs = X + slot[j] * n;
+  double* rs = res + slot[j] * n;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ev = (double)e[j * n + i];
+    xs[i] += ev;
+    const double rv = rs[i] - ((double)ae[j * n + i] + sg * ev);
+    rs[i] = rv;
+    acc += rv * rv;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[j * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_gather_done(const MsState* __restrict__ st, int nsys, int* out) {
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) out[s] = st[s].done;
 }
 
 // ----------------------------------------------------------------- precision / algebra helpers
@@ -335,6 +388,10 @@ struct DevBuf {
     }
     return BRI_OK;
   }
+  void reset() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
   template <typename T> T* as() const { return (T*)p; }
 };
 
@@ -365,7 +422,8 @@ struct Counters {
 // sig: host [nsys][nshift], increasing within a system.
 template <typename R>
 int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, const double* sig, const R* b, R* x,
-                     double tol, int maxiter, int* iters_out, Counters* cnt) {
+                     double tol, int maxiter, int* iters_out, Counters* cnt, const double* tols,
+                     double* lam_out = nullptr) {
   using T = typename P2<R>::T;
   cudaStream_t st = c->stream;
   const int64_t n2 = c->g.V * 12;  // complex pairs per system
@@ -393,7 +451,8 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
     h.nshift = nshift;
     h.sig_base = sig[s * nshift];
     for (int k = 0; k < nshift; ++k) h.delta[k] = sig[s * nshift + k] - h.sig_base;
-    h.tol2 = tol * tol;
+    const double ts = tols ? tols[s] : tol;
+    h.tol2 = ts * ts;
     h.maxiter = maxiter;
   }
   BRI_CUDA(cudaMemcpyAsync(S, hs.data(), sizeof(MsState) * nsys, cudaMemcpyHostToDevice, st));
@@ -405,26 +464,33 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
   int* hdone = (int*)c->host_pinned;  // pinned scratch, >= 4 KB
   const int check_every = 8;
   int it = 0;
-  bool all_done = false;
-  while (!all_done && it < maxiter) {
+  // Systems [nact, nsys) have all converged: the stencil and the vector
+  // kernels only run over the prefix [0, nact) (callers put the hardest
+  // systems first).  Converged systems inside the prefix are skipped by the
+  // vector kernels through their done flags.
+  int nact = nsys;
+  DevBuf bflags;
+  if ((rc = bflags.alloc(sizeof(int) * nsys, st))) return rc;
+  while (nact > 0 && it < maxiter) {
+    dim3 vga(nblk, nact);
     for (int j = 0; j < check_every && it < maxiter; ++j, ++it) {
-      if ((rc = dirac_bri(c, t, p, nsys, m0, 0, oprec, st))) return rc;
-      if ((rc = dirac_bri(c, q, t, nsys, m0, 1, oprec, st))) return rc;
+      if ((rc = dirac_bri(c, t, p, nact, m0, 0, oprec, st))) return rc;
+      if ((rc = dirac_bri(c, q, t, nact, m0, 1, oprec, st))) return rc;
       cnt->matvecs += 2;
       if (sizeof(R) == 8) cnt->matvecs64 += 2;
-      k_shift_dot<R><<<vg, RED_THREADS, 0, st>>>(n2, S, p, q, part); note_launch();
-      k_scalar_alpha<<<nsys, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
-      k_update_xr<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, S, q, r, p, (T*)x, part); note_launch();
-      k_scalar_beta<<<nsys, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
-      k_update_p<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, S, r, p); note_launch();
+      k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q, part); note_launch();
+      k_scalar_alpha<<<nact, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q, r, p, (T*)x, part, it == 0 ? 1 : 0);
+      note_launch();
+      k_scalar_beta<<<nact, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      k_update_p0<R><<<vga, RED_THREADS, 0, st>>>(n2, S, r, p); note_launch();
     }
     BRI_LAUNCH_CHECK("multishift iteration");
-    // poll the done flags of all systems
-    for (int s = 0; s < nsys; ++s)
-      BRI_CUDA(cudaMemcpyAsync(hdone + 2 * s, &S[s].done, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    // poll the done flags
+    k_gather_done<<<1, 256, 0, st>>>(S, nsys, bflags.as<int>()); note_launch();
+    BRI_CUDA(cudaMemcpyAsync(hdone, bflags.as<int>(), sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     BRI_CUDA(cudaStreamSynchronize(st));
-    all_done = true;
-    for (int s = 0; s < nsys; ++s) all_done = all_done && hdone[2 * s];
+    while (nact > 0 && hdone[nact - 1]) --nact;
   }
   BRI_CUDA(cudaMemcpyAsync(hs.data(), S, sizeof(MsState) * nsys, cudaMemcpyDeviceToHost, st));
   BRI_CUDA(cudaStreamSynchronize(st));
@@ -435,6 +501,11 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
     if (hs[s].active[0] && !hs[s].error) notconv = 1;
   }
   *iters_out = maxit;
+  if (lam_out) {
+    double lm = 0.0;
+    for (int s = 0; s < nsys; ++s) lm = std::max(lm, hs[s].lam_max - hs[s].sig_base);
+    *lam_out = lm;
+  }
   if (err) {
     set_error("multi-shift CG: non-finite or non-positive curvature in a reduction");
     return BRI_ERR_NONFINITE;
@@ -482,93 +553,162 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   for (int s = 0; s < nrhs; ++s)
     for (int k = 0; k < n; ++k) sig_all[(size_t)s * n + k] = sig[k];
 
+  double tph[4] = {0, 0, 0, 0};
+  auto tnow = [&]() {
+    cudaStreamSynchronize(st);
+    return std::chrono::steady_clock::now();
+  };
+  auto tmark = tnow();
+  auto lap = [&](int ph) {
+    auto t1 = tnow();
+    tph[ph] += std::chrono::duration<double>(t1 - tmark).count();
+    tmark = t1;
+  };
   DevBuf bX;
   if ((rc = bX.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
   double* X = bX.as<double>();
   int solve_rc = BRI_OK;
 
   if (prec == BRI_PREC_F64) {
-    solve_rc = multishift_solve<double>(c, prec, m0, nrhs, n, sig_all.data(), b, X, tol, maxiter, &iters, &cnt);
+    solve_rc = multishift_solve<double>(c, prec, m0, nrhs, n, sig_all.data(), b, X, tol, maxiter, &iters, &cnt,
+                                        nullptr);
     if (solve_rc < 0) return solve_rc;
+    lap(0);
   } else if (prec == BRI_PREC_F32 || prec == BRI_PREC_F32_BF16) {
-    // phase 1: FP32 multi-shift
+    // phase 1: FP32 multi-shift (FP64 scalars and reductions)
     DevBuf bb32, bx32;
     if ((rc = bb32.alloc(sizeof(float) * nreal * nrhs, st))) return rc;
     if ((rc = bx32.alloc(sizeof(float) * nreal * nrhs * n, st))) return rc;
     k_convert<double, float><<<1024, 256, 0, st>>>(nreal * nrhs, b, bb32.as<float>()); note_launch();
     const double tol1 = std::max(tol, 1e-6);
     int it1 = 0;
+    double lam_est = 0.0;
     rc = multishift_solve<float>(c, prec, m0, nrhs, n, sig_all.data(), bb32.as<float>(), bx32.as<float>(), tol1,
-                                 maxiter, &it1, &cnt);
+                                 maxiter, &it1, &cnt, nullptr, &lam_est);
+    lam_est = 1.1 * lam_est + 1e-3;
     if (rc < 0) return rc;
     iters = it1;
     k_convert<float, double><<<1024, 256, 0, st>>>(nreal * nrhs * n, bx32.as<float>(), X); note_launch();
     BRI_LAUNCH_CHECK("convert");
-    // phase 2: defect correction per shift
+    bb32.reset();
+    bx32.reset();
+    lap(0);
+    // phase 2: one FP64 residual per (shift, rhs), r_i = b - (A + sigma_i) X_i
     DevBuf btmp1, btmp2, bpart, bdsum, bres;
     if ((rc = btmp1.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
     if ((rc = btmp2.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-    const int nblk_r = grid_for(nreal / 2, nrhs);
-    if ((rc = bpart.alloc(sizeof(double) * nblk_r * nrhs, st))) return rc;
-    if ((rc = bdsum.alloc(sizeof(double) * nrhs, st))) return rc;
-    std::vector<double> bn2(nrhs), rn2(nrhs);
-    {  // ||b||^2
-      k_residual<<<dim3(nblk_r, nrhs), RED_THREADS, 0, st>>>(nreal, b, b, b, -1.0, nullptr, bpart.as<double>()); note_launch();
-      // b - b - (-1) b = b
-      k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
-      BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-      BRI_CUDA(cudaStreamSynchronize(st));
+    const int nblk_r = grid_for(nreal / 2, std::max(nrhs, 32));
+    if ((rc = bpart.alloc(sizeof(double) * nblk_r * std::max(nrhs, 32), st))) return rc;
+    if ((rc = bdsum.alloc(sizeof(double) * std::max(nrhs, 32), st))) return rc;
+    if ((rc = bres.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
+    std::vector<double> bn2(nrhs), rn2((size_t)n * nrhs), tmp(std::max(nrhs, 32));
+    std::vector<double> err_acc((size_t)n * nrhs, 0.0);  // accumulated FP32 tracking error bound per slot
+    k_residual<<<dim3(nblk_r, nrhs), RED_THREADS, 0, st>>>(nreal, b, b, b, -1.0, nullptr, bpart.as<double>());
+    note_launch();
+    k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
+    BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    BRI_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < n; ++k) {
+      rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k],
+                      bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(), btmp2.as<double>(),
+                      bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+      if (rc) return rc;
+      for (int s = 0; s < nrhs; ++s) rn2[(size_t)k * nrhs + s] = tmp[s];
     }
-    const int max_rounds = 8;
+    btmp1.reset();
+    btmp2.reset();
+    lap(1);
+    // phase 3: FP32 defect correction of every shift still above tol; the
+    // residual is then updated with the FP32 operator applied to the small
+    // correction (its rounding error is ~1e-7 of the old residual).
+    const int max_rounds = 6;
     for (int round = 0; round < max_rounds; ++round) {
-      // FP64 residuals of every (shift, rhs); collect the unconverged ones
-      std::vector<int> todo_k, todo_s;
-      std::vector<double> todo_sig;
-      if ((rc = bres.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
-      double worst = 0.0;
-      for (int k = 0; k < n; ++k) {
-        rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k],
-                        bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(), btmp2.as<double>(),
-                        bpart.as<double>(), bdsum.as<double>(), rn2.data(), &cnt);
-        if (rc) return rc;
-        for (int s = 0; s < nrhs; ++s) {
-          double rel = std::sqrt(rn2[s] / std::max(bn2[s], 1e-300));
-          worst = std::max(worst, rel);
-          if (rel > tol) {
-            todo_k.push_back(k);
-            todo_s.push_back(s);
-            todo_sig.push_back(sig[k]);
+      std::vector<int> todo;  // slot = k * nrhs + s, hardest (smallest shift) first
+      for (int k = 0; k < n; ++k)
+        for (int sidx = 0; sidx < nrhs; ++sidx) {
+          const size_t slot = (size_t)k * nrhs + sidx;
+          if (std::sqrt(rn2[slot] / std::max(bn2[sidx], 1e-300)) > tol) todo.push_back((int)slot);
+        }
+      if (todo.empty()) break;
+      if (round == max_rounds - 1) {
+        solve_rc = BRI_NOT_CONVERGED;
+        break;
+      }
+      refinements++;
+      const int chunk = 32;
+      for (size_t c0i = 0; c0i < todo.size(); c0i += chunk) {
+        const int m = (int)std::min<size_t>(chunk, todo.size() - c0i);
+        std::vector<double> msig(m), mtol(m);
+        std::vector<long long> slots(m);
+        for (int j = 0; j < m; ++j) {
+          const int slot = todo[c0i + j], k = slot / nrhs, sidx = slot % nrhs;
+          msig[j] = sig[k];
+          slots[j] = slot;
+          const double ratio = tol * std::sqrt(bn2[sidx] / std::max(rn2[slot], 1e-300));
+          mtol[j] = std::min(0.5, std::max(1e-6, 0.3 * ratio));
+        }
+        DevBuf brhs, bsol, bt1, bt2, bslot, bsig;
+        if ((rc = brhs.alloc(sizeof(float) * nreal * m, st))) return rc;
+        if ((rc = bsol.alloc(sizeof(float) * nreal * m, st))) return rc;
+        if ((rc = bslot.alloc(sizeof(long long) * m, st))) return rc;
+        if ((rc = bsig.alloc(sizeof(double) * m, st))) return rc;
+        BRI_CUDA(cudaMemcpyAsync(bslot.as<long long>(), slots.data(), sizeof(long long) * m,
+                                 cudaMemcpyHostToDevice, st));
+        BRI_CUDA(cudaMemcpyAsync(bsig.as<double>(), msig.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+        k_gather_f32<<<dim3(512, m), 256, 0, st>>>(nreal, bres.as<double>(), bslot.as<long long>(),
+                                                   brhs.as<float>()); note_launch();
+        int itc = 0;
+        // Corrections always use FP32 links: with BF16 links the operator error
+        // (~4e-3 relative) times the condition number of the small shifts
+        // exceeds one, so a BF16 correction would not reduce the residual.
+        rc = multishift_solve<float>(c, BRI_PREC_F32, m0, m, 1, msig.data(), brhs.as<float>(), bsol.as<float>(),
+                                     1e-5, maxiter, &itc, &cnt, mtol.data());
+        if (rc < 0) return rc;
+        // X += e (FP64); r -= (A + sigma) e with the FP32 operator
+        if ((rc = bt1.alloc(sizeof(float) * nreal * m, st))) return rc;
+        if ((rc = bt2.alloc(sizeof(float) * nreal * m, st))) return rc;
+        // (FP32 links even when the solve used BF16 ones: the update must be
+        // accurate to ~1e-7 of the old residual)
+        if ((rc = dirac_bri(c, bt1.as<float>(), bsol.as<float>(), m, m0, 0, BRI_PREC_F32, st))) return rc;
+        if ((rc = dirac_bri(c, bt2.as<float>(), bt1.as<float>(), m, m0, 1, BRI_PREC_F32, st))) return rc;
+        cnt.matvecs += 2;
+        const int nblk_u = grid_for(nreal / 2, m);
+        k_correct<<<dim3(nblk_u, m), RED_THREADS, 0, st>>>(nreal, bslot.as<long long>(), bsig.as<double>(),
+                                                          bsol.as<float>(), bt2.as<float>(), X, bres.as<double>(),
+                                                          bpart.as<double>()); note_launch();
+        k_sum_partials<<<m, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_u, bdsum.as<double>()); note_launch();
+        BRI_LAUNCH_CHECK("refinement update");
+        BRI_CUDA(cudaMemcpyAsync(tmp.data(), bdsum.as<double>(), sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        BRI_CUDA(cudaStreamSynchronize(st));
+        // The FP32-tracked residual is trusted only where its rounding error,
+        // ~eps32 kappa_i ||r_old|| with kappa_i = (lambda_max + sigma_i)/sigma_i,
+        // is well below tol; otherwise the residual is recomputed in FP64.
+        std::vector<int> verify;
+        for (int j = 0; j < m; ++j) {
+          const int slot = (int)slots[j], k = slot / nrhs, sidx = slot % nrhs;
+          const double kappa = (lam_est + sig[k]) / sig[k];
+          err_acc[slot] += 2e-7 * kappa * std::sqrt(rn2[slot]);
+          const double goal = tol * std::sqrt(bn2[sidx]);
+          rn2[slot] = tmp[j];
+          if (err_acc[slot] > 0.25 * goal && std::sqrt(rn2[slot]) <= goal) verify.push_back(slot);
+        }
+        if (!verify.empty()) {
+          DevBuf v1, v2;
+          if ((rc = v1.alloc(sizeof(double) * nreal, st))) return rc;
+          if ((rc = v2.alloc(sizeof(double) * nreal, st))) return rc;
+          for (int slot : verify) {
+            const int k = slot / nrhs, sidx = slot % nrhs;
+            rc = residual64(c, m0, 1, b + (int64_t)sidx * nreal, X + (int64_t)slot * nreal, sig[k],
+                            bres.as<double>() + (int64_t)slot * nreal, v1.as<double>(), v2.as<double>(),
+                            bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+            if (rc) return rc;
+            rn2[slot] = tmp[0];
+            err_acc[slot] = 0.0;
           }
         }
       }
-      if (todo_k.empty()) break;
-      refinements++;
-      // batched FP32 correction solves, one system per unconverged (shift, rhs)
-      const int ns = (int)todo_k.size();
-      const int chunk = 32;
-      for (int c0i = 0; c0i < ns; c0i += chunk) {
-        const int m = std::min(chunk, ns - c0i);
-        DevBuf brhs, bsol;
-        if ((rc = brhs.alloc(sizeof(float) * nreal * m, st))) return rc;
-        if ((rc = bsol.alloc(sizeof(float) * nreal * m, st))) return rc;
-        for (int j = 0; j < m; ++j) {
-          const int k = todo_k[c0i + j], s = todo_s[c0i + j];
-          k_convert<double, float><<<512, 256, 0, st>>>(
-              nreal, bres.as<double>() + ((int64_t)k * nrhs + s) * nreal, brhs.as<float>() + (int64_t)j * nreal); note_launch();
-        }
-        int itc = 0;
-        rc = multishift_solve<float>(c, prec, m0, m, 1, todo_sig.data() + c0i, brhs.as<float>(), bsol.as<float>(),
-                                     1e-5, maxiter, &itc, &cnt);
-        if (rc < 0) return rc;
-        for (int j = 0; j < m; ++j) {
-          const int k = todo_k[c0i + j], s = todo_s[c0i + j];
-          k_accumulate<<<512, 256, 0, st>>>(nreal, X + ((int64_t)k * nrhs + s) * nreal,
-                                            bsol.as<float>() + (int64_t)j * nreal); note_launch();
-        }
-        BRI_LAUNCH_CHECK("refinement accumulate");
-      }
-      if (round == max_rounds - 1) solve_rc = BRI_NOT_CONVERGED;
     }
+    lap(2);
   } else {
     set_error("sign_apply_multishift: unknown precision");
     return BRI_ERR_INVALID;
@@ -613,6 +753,7 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   cnt.matvecs += 1;
   cnt.matvecs64 += 1;
   k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), (double*)y); note_launch();
+  lap(3);
   BRI_LAUNCH_CHECK("k_axpby");
   BRI_CUDA(cudaStreamSynchronize(st));
   if (stats) {
@@ -622,6 +763,7 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
     stats->refinements = refinements;
     stats->n_shifts = n;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int ph = 0; ph < 4; ++ph) stats->phase_seconds[ph] = tph[ph];
   }
   return solve_rc;
 }

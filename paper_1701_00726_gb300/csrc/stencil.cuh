@@ -1,0 +1,119 @@
+// Device helpers shared by the Brillouin and Wilson stencil kernels.
+#pragma once
+
+#include "internal.cuh"
+#include "cplx.cuh"
+
+namespace bri {
+
+template <typename R> struct Spinor {
+  C<R> v[4][3];
+};
+
+// AoS spinor [4][3] complex: 24 reals, 16-byte vector loads.
+__device__ __forceinline__ void load_spinor(Spinor<float>& s, const float* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float4 v = __ldg(q + i);
+    int e0 = 2 * i, e1 = 2 * i + 1;  // complex element index 0..11
+    s.v[e0 / 3][e0 % 3] = C<float>{v.x, v.y};
+    s.v[e1 / 3][e1 % 3] = C<float>{v.z, v.w};
+  }
+}
+__device__ __forceinline__ void load_spinor(Spinor<double>& s, const double* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    double2 v = __ldg(q + e);
+    s.v[e / 3][e % 3] = C<double>{v.x, v.y};
+  }
+}
+__device__ __forceinline__ void store_spinor(float* p, const Spinor<float>& s) {
+  float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    int e0 = 2 * i, e1 = 2 * i + 1;
+    q[i] = make_float4(s.v[e0 / 3][e0 % 3].re, s.v[e0 / 3][e0 % 3].im, s.v[e1 / 3][e1 % 3].re,
+                       s.v[e1 / 3][e1 % 3].im);
+  }
+}
+__device__ __forceinline__ void store_spinor(double* p, const Spinor<double>& s) {
+  double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+  for (int e = 0; e < 12; ++e) q[e] = make_double2(s.v[e / 3][e % 3].re, s.v[e / 3][e % 3].im);
+}
+
+template <typename R> __device__ __forceinline__ void zero(Spinor<R>& s) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) s.v[a][b] = C<R>{0, 0};
+}
+
+// One 3x3 link in structure-of-arrays storage: element e of the link at site
+// n sits at p[e*V] (p already offset by n).
+template <typename R, typename LS>
+__device__ __forceinline__ void load_link(C<R> w[3][3], const LS* __restrict__ p, int V) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    if constexpr (sizeof(R) == 8) {
+      w[e / 3][e % 3] = ld2(reinterpret_cast<const double2*>(p) + e * V);
+    } else {
+      C<float> f = ld2(p + e * V);
+      w[e / 3][e % 3] = C<R>{(R)f.re, (R)f.im};
+    }
+  }
+}
+
+__device__ __forceinline__ int wrap(int c, int L) { return c < 0 ? c + L : (c >= L ? c - L : c); }
+
+// Packed Hermitian 6x6 times a 6-vector: diag reals [0..5], then upper complex.
+template <typename R>
+__device__ __forceinline__ void clover_block(C<R> out[6], const R* __restrict__ cl, int64_t V, int64_t n,
+                                             const C<R> in[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    R d = __ldg(cl + (int64_t)i * V + n);
+    out[i] = C<R>{d * in[i].re, d * in[i].im};
+  }
+  int k = 6;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) {
+      C<R> cij{__ldg(cl + (int64_t)k * V + n), __ldg(cl + (int64_t)(k + 1) * V + n)};
+      cfma(out[i], cij, in[j]);
+      cfma_cj(out[j], cij, in[i]);
+      k += 2;
+    }
+}
+
+// acc += C(n) x, C the two chiral 6x6 clover blocks.
+template <typename R>
+__device__ __forceinline__ void add_clover(Spinor<R>& acc, const Spinor<R>& x, const R* __restrict__ cl,
+                                           int64_t V, int64_t n) {
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk) {
+    C<R> in[6], out[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) in[i] = x.v[2 * blk + i / 3][i % 3];
+    clover_block(out, cl + (int64_t)blk * 36 * V, V, n, in);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc.v[2 * blk + i / 3][i % 3] = acc.v[2 * blk + i / 3][i % 3] + out[i];
+  }
+}
+
+// Whether FP32 stencils carry two right-hand sides per thread (shared link
+// loads); BRI_PAIR_RHS=0 turns it off.
+int pair_rhs_enabled();
+
+// Host-side launchers (one translation unit per precision).
+template <typename R, typename LS>
+int launch_bri_t(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, int nrhs, int dagger,
+                 cudaStream_t s);
+template <typename R, typename LS>
+int launch_wil_t(const Geom& g, R* y, const R* x, const LS* U, const R* cl, R diag, int nrhs, int dagger,
+                 cudaStream_t s);
+
+}  // namespace bri

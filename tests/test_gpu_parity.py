@@ -184,3 +184,19 @@ def test_bri_apply_full_size_sampled():
     lhs = torch.vdot(phi.flatten(), lat.bri_apply(psi, -1.0).flatten())
     rhs = torch.vdot(lat.bri_apply(phi, -1.0, dagger=True).flatten(), psi.flatten())
     assert abs((lhs - rhs).item()) < 1e-11 * abs(lhs.item())
+
+
+@pytest.mark.parametrize("prec", [PREC_F32, PREC_F32_BF16])
+def test_mixed_order16_true_residuals(prec):
+    """KL order 16 (smallest shift 2.3e-3), stout-smeared field, c_SW = 1: every shift's FP64
+    true residual reaches the requested 1e-10 and D_ov agrees with the FP64 GPU path."""
+    dims = (8, 8, 8, 8)
+    u = sf.gauge_field(dims, 1, 0.1, 3)
+    x = sf.gaussian_source(dims, 3, 1001)
+    lat = _lattice(dims, u, 1.0)
+    xt = torch.from_numpy(x).cuda()
+    y, st = lat.overlap_apply(xt, n=16, rho=1.0, tol=1e-10, prec=prec, want_true_residual=True)
+    assert st["converged"]
+    assert st["max_true_residual"] <= 1e-10
+    y64, st64 = lat.overlap_apply(xt, n=16, rho=1.0, tol=1e-12, prec=PREC_F64)
+    assert relerr(y.cpu().numpy(), y64.cpu().numpy()) < 1e-9
