@@ -35,6 +35,7 @@
 #include <vector>
 
 namespace bri {
+
 namespace {
 
 constexpr int NS = BRI_MAX_SHIFTS;
