@@ -134,6 +134,26 @@ int sign_apply_multishift(bri_ctx* ctx, void* y, const void* x, int nrhs, int n,
 int overlap_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
                   double rho, double am, double scale, double tol, int prec, bri_stats* st);
 
+/* The FP64 sign-function solve of sign_apply_multishift (prec BRI_PREC_F64)
+ * without any device allocation, for callers that cannot call cudaMalloc at
+ * apply time (device memory fully reserved by their own pool, or loops where
+ * an implicitly synchronising allocation is not acceptable).  There is no
+ * counterpart in the paper; it is a deployment convenience.
+ *
+ * All solver workspace comes from one 32 MiB static device array that every
+ * device loading the library holds until exit.  Limit: V * nrhs * (2n + 3) *
+ * 192 bytes plus ~64 KB of state must fit in it (e.g. 8^4 with nrhs = 1 and
+ * n <= 20, or 4^4 with nrhs <= 16 at n = 16); larger problems are rejected
+ * with BRI_ERR_INVALID and a message.  The first call on a device looks the
+ * array's address up (cudaGetSymbolAddress) and should come before any stream
+ * capture.  Every call reuses the same array and leaves its contents behind;
+ * the solver initialises everything it reads, but two calls whose work
+ * overlaps on one device (other streams or host threads) race on it.
+ * x, y: device complex128 [nrhs][V][4][3]; st may be NULL (true residuals are
+ * not computed here). */
+int sign_apply_multishift_noalloc(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
+                                  double rho, double scale, double tol, bri_stats* st);
+
 /* Profiling (tracing) of the stencil kernels.  When enabled, every launch of
  * the Brillouin (op 0) or Wilson (op 1) stencil, including those issued inside
  * the solvers, is bracketed by CUDA events on the context stream.

@@ -145,6 +145,22 @@ class Lattice:
         d["converged"] = rc == 0
         return y, d
 
+    def sign_apply_noalloc(self, x, n, rho=1.0, tol=1e-12, kind=KL_DIAGONAL, scale=1.0, out=None):
+        """FP64 gamma5 f_nn(H) x through the entry point that allocates no device memory
+        (its workspace is a fixed 32 MiB device array).  ``out`` lets the caller keep
+        allocation out of this call too.  Returns (y, stats)."""
+        torch = _torch()
+        nrhs = self._spinor(x, (torch.complex128,))
+        y = torch.empty_like(x) if out is None else out
+        st = self._solver_stats(False, 0)
+        rc = self.lib.sign_apply_multishift_noalloc(self._h, ctypes.c_void_p(y.data_ptr()),
+                                                    ctypes.c_void_p(x.data_ptr()), nrhs, int(n), int(kind),
+                                                    float(rho), float(scale), float(tol), ctypes.byref(st))
+        _lib.check(rc, "sign_apply_multishift_noalloc")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return y, d
+
     def overlap_apply(self, x, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL, scale=1.0,
                       want_true_residual=False, maxiter=0, out=None):
         """(1 - am/(2 rho)) D_ov x + am x with D_ov = rho (1 + gamma5 f_nn(H)).  Returns (y, stats)."""

@@ -75,6 +75,9 @@ _SIGS = {
     "overlap_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(BriStats)]),
+    "sign_apply_multishift_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_double, ctypes.POINTER(BriStats)]),
     "bri_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bri_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),

@@ -98,6 +98,17 @@ int dirac_bri(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagge
 int dirac_wil(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
               cudaStream_t s);
 
+// Device scratch from a caller-provided block (used by the entry point that
+// allocates nothing); when no arena is set the solvers allocate from the
+// stream-ordered pool.  Thread-local, so concurrent host threads do not mix.
+struct ScratchArena {
+  char* base;
+  size_t cap;
+  size_t used;
+};
+void set_current_arena(ScratchArena* a);
+ScratchArena* current_arena();
+
 // host-side KL coefficients
 int kl_host(int n, int kind, double scale, double* c0, double* w, double* sigma);
 

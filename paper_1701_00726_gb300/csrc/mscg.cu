@@ -36,6 +36,10 @@
 
 namespace bri {
 
+static thread_local ScratchArena* t_arena = nullptr;
+void set_current_arena(ScratchArena* a) { t_arena = a; }
+ScratchArena* current_arena() { return t_arena; }
+
 namespace {
 
 constexpr int NS = BRI_MAX_SHIFTS;
@@ -367,19 +371,41 @@ int grid_for(int64_t n, int nsys) {
 struct DevBuf {
   void* p = nullptr;
   cudaStream_t s = nullptr;
+  ScratchArena* arena = nullptr;  // set when carved from a caller-provided arena
+  size_t arena_mark = 0;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, s);
+  ~DevBuf() { release(); }
+  void release() {
+    if (!p) return;
+    if (arena) {
+      // stack discipline: give the space back when this is the newest block
+      if (arena->used == arena_mark + ((arena_bytes + 255) & ~size_t(255))) arena->used = arena_mark;
+      arena = nullptr;
+    } else {
+      cudaFreeAsync(p, s);
+    }
+    p = nullptr;
   }
+  size_t arena_bytes = 0;
   int alloc(size_t bytes, cudaStream_t st) {
     s = st;
-    if (p) {
-      cudaFreeAsync(p, s);
-      p = nullptr;
-    }
+    release();
     if (bytes == 0) bytes = 16;
+    if (ScratchArena* a = current_arena()) {
+      const size_t need = (bytes + 255) & ~size_t(255);
+      if (a->used + need > a->cap) {
+        set_error("no-allocation scratch exhausted: the problem is larger than the static scratch array");
+        return BRI_ERR_INVALID;
+      }
+      arena = a;
+      arena_mark = a->used;
+      arena_bytes = bytes;
+      p = a->base + a->used;
+      a->used += need;
+      return BRI_OK;
+    }
     cudaError_t e = cudaMallocAsync(&p, bytes, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -389,10 +415,7 @@ struct DevBuf {
     }
     return BRI_OK;
   }
-  void reset() {
-    if (p) cudaFreeAsync(p, s);
-    p = nullptr;
-  }
+  void reset() { release(); }
   template <typename T> T* as() const { return (T*)p; }
 };
 
