@@ -63,7 +63,37 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="also time one plain FP64 D_ov (1 rhs) outside the timed region")
+    ap.add_argument("--stencil-probe", default=None, metavar="LX,LY,LZ,LT",
+                    help="profiling helper: only launch the FP32 Brillouin stencil on this lattice and print "
+                         "its CUDA-event time (used for the ncu captures under profiles/)")
+    ap.add_argument("--probe-nrhs", type=int, default=1)
+    ap.add_argument("--probe-launches", type=int, default=4)
     return ap.parse_args()
+
+
+def stencil_probe(args):
+    import torch
+
+    import synthetic_fields as sf
+    from paper_1701_00726_gb300 import Lattice
+    dims = tuple(int(v) for v in args.stencil_probe.split(","))
+    vol = dims[0] * dims[1] * dims[2] * dims[3]
+    lat = Lattice(dims)
+    lat.build_links(torch.from_numpy(sf.gauge_field(dims, 1, eps=0.5, device="cuda")).cuda(), C_SW)
+    x = torch.randn((args.probe_nrhs, vol * 12), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    lat.bri_apply(x, -RHO, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.probe_launches):
+        lat.bri_apply(x, -RHO, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.probe_launches
+    byt = vol * (LINK_BYTES[1] + CLOVER_BYTES + SPINOR_BYTES * args.probe_nrhs)
+    print(json.dumps({"stencil_probe": list(dims), "nrhs": args.probe_nrhs, "ms": ms,
+                      "alg_GBps": byt / ms / 1e6}), flush=True)
 
 
 def dist_env():
@@ -90,18 +120,24 @@ def measured_peak():
 def stencil_traffic():
     """dram bytes per launch of the FP32 stencil from the committed ncu summary,
     valid only while the stencil source is unchanged (hash match)."""
-    src = os.path.join(ROOT, "paper_1701_00726_gb300", "csrc", "dirac.cu")
-    p = os.path.join(ROOT, "profiles", "bri_stencil_traffic.json")
+    p = os.path.join(ROOT, "profiles", "bri_stencil_traffic.txt")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("dirac_cu_sha256_16") != h:
+        if d.get("stencil_source_sha256_16") != stencil_source_hash():
             return None
         return d
     except Exception:
         return None
+
+
+def stencil_source_hash():
+    """Hash of the FP32 stencil's sources (kernel header and shared helpers)."""
+    h = hashlib.sha256()
+    for f in ("bri_kernel.cuh", "stencil.cuh", "cplx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1701_00726_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -193,6 +229,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.stencil_probe:
+        stencil_probe(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

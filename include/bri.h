@@ -134,6 +134,37 @@ int sign_apply_multishift(bri_ctx* ctx, void* y, const void* x, int nrhs, int n,
 int overlap_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
                   double rho, double am, double scale, double tol, int prec, bri_stats* st);
 
+/* Massive overlap solve D_m x = b (Secs. 4.2-4.4) with cascaded
+ * preconditioning (Sec. 8, Eqs. cascaded_one, cascaded_two): solves
+ * (D_ov + mt) x = bt, mt = am/(1 - am/(2 rho)), with bt of the traditional
+ * form (complete = 0, Eq. upshot_traditional) or of the complete form
+ * (complete = 1, Eq. upshot_complete), D_ov of Kenney-Laub order n_outer, by
+ * right-preconditioned BiCGstab to relative residual tol.  n_inner > 0 adds
+ * the cascade: the preconditioner is an inexact solve (relative 1e-2) with the
+ * order-n_inner operator, itself preconditioned by an inexact solve with the
+ * kernel D_{-rho} + (1 + mt/rho); n_inner = 0 runs unpreconditioned.
+ * x, b: device complex128 [nrhs][V][4][3], x overwritten (initial guess 0).
+ * st (may be NULL): iterations = outer BiCGstab iterations (max over rhs),
+ * refinements = inner iterations (sum), matvecs = kernel applications,
+ * max_true_residual = final FP64 relative residual of the outer system. */
+int overlap_solve(bri_ctx* ctx, void* x, const void* b, int nrhs, int n_outer, int n_inner, int kind,
+                  double rho, double am, int complete, double tol, int prec, bri_stats* st);
+
+/* Adjoint of overlap_apply for L = sum_r Re <eta_r, D_m psi_r>,
+ * D_m = (1 - am/(2 rho)) D_ov + am (Eqs. def_over, def_mass_traditional;
+ * Sec. 9: with a fixed-order rational the inner derivative is explicit).
+ * Writes g_psi = D_m^dagger eta = gamma5 D_m gamma5 eta ([nrhs][V][4][3]
+ * complex128) and g_U = dL/dU for the thin links given to bri_build_links
+ * ([V][4][3][3] complex128), with the conventions dL = Re<g_psi, dpsi> and
+ * dL = Re sum tr(g_U^dagger dU) (those of PyTorch's complex autograd).  The
+ * derivative runs through the multi-shift solves (x_i for psi and z_i for
+ * D^dagger eta, same shifts) and the path-averaged link construction (App. C).
+ * The clover term is not differentiated: the links must have been built with
+ * c_sw = 0 (BRI_ERR_INVALID otherwise).  prec as for overlap_apply (solves);
+ * the force and link back-propagation run in FP64. */
+int overlap_grad(bri_ctx* ctx, void* g_psi, void* g_U, const void* eta, const void* psi, int nrhs, int n,
+                 int kind, double rho, double am, double scale, double tol, int prec, bri_stats* st);
+
 /* The FP64 sign-function solve of sign_apply_multishift (prec BRI_PREC_F64)
  * without any device allocation, for callers that cannot call cudaMalloc at
  * apply time (device memory fully reserved by their own pool, or loops where

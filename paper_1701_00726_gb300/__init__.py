@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KL_DIAGONAL, KL_UPPER, PREC_F32, PREC_F32_BF16, PREC_F64,
                    BriError, BriStats, kl_coeffs)
 
-__all__ = ["Lattice", "kl_coeffs", "BriError", "BriStats", "PREC_F64", "PREC_F32", "PREC_F32_BF16",
+__all__ = ["Lattice", "overlap", "OverlapFunction", "kl_coeffs", "BriError", "BriStats", "PREC_F64", "PREC_F32", "PREC_F32_BF16",
            "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T"]
 
 
@@ -145,6 +145,43 @@ class Lattice:
         d["converged"] = rc == 0
         return y, d
 
+    def overlap_solve(self, b, n_outer, n_inner=0, rho=1.0, am=0.0, complete=True, tol=1e-12, prec=PREC_F64,
+                      kind=KL_DIAGONAL, maxiter=0, out=None):
+        """Solve D_m x = b (traditional or complete massive overlap) by BiCGstab with the
+        cascaded preconditioner of order n_inner (0: none).  Returns (x, stats)."""
+        torch = _torch()
+        nrhs = self._spinor(b, (torch.complex128,))
+        x = torch.empty_like(b) if out is None else out
+        st = self._solver_stats(False, maxiter)
+        rc = self.lib.overlap_solve(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(b.data_ptr()), nrhs,
+                                    int(n_outer), int(n_inner), int(kind), float(rho), float(am), int(bool(complete)),
+                                    float(tol), int(prec), ctypes.byref(st))
+        _lib.check(rc, "overlap_solve")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return x, d
+
+    def overlap_grad(self, eta, psi, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL, scale=1.0,
+                     maxiter=0):
+        """Adjoint of overlap_apply for L = sum_r Re<eta_r, D_m psi_r>: returns (g_psi, g_U, stats),
+        g_U with the shape [Lt, Lz, Ly, Lx, 4, 3, 3] of the gauge field (links built with c_sw = 0)."""
+        torch = _torch()
+        nrhs = self._spinor(psi, (torch.complex128,))
+        if self._spinor(eta, (torch.complex128,)) != nrhs:
+            raise BriError("eta and psi must hold the same number of right-hand sides")
+        g_psi = torch.empty_like(psi)
+        lt, lz, ly, lx = self.dims[3], self.dims[2], self.dims[1], self.dims[0]
+        g_u = torch.empty((lt, lz, ly, lx, 4, 3, 3), dtype=torch.complex128, device=psi.device)
+        st = self._solver_stats(False, maxiter)
+        rc = self.lib.overlap_grad(self._h, ctypes.c_void_p(g_psi.data_ptr()), ctypes.c_void_p(g_u.data_ptr()),
+                                   ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(psi.data_ptr()), nrhs, int(n),
+                                   int(kind), float(rho), float(am), float(scale), float(tol), int(prec),
+                                   ctypes.byref(st))
+        _lib.check(rc, "overlap_grad")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return g_psi, g_u, d
+
     def sign_apply_noalloc(self, x, n, rho=1.0, tol=1e-12, kind=KL_DIAGONAL, scale=1.0, out=None):
         """FP64 gamma5 f_nn(H) x through the entry point that allocates no device memory
         (its workspace is a fixed 32 MiB device array).  ``out`` lets the caller keep
@@ -175,3 +212,42 @@ class Lattice:
         d = st.as_dict()
         d["converged"] = rc == 0
         return y, d
+
+
+class OverlapFunction:
+    """torch.autograd.Function for y = D_m psi with gradients for psi and the gauge field.
+
+    Built lazily so that importing the package does not import torch.
+    """
+
+    _fn = None
+
+    @classmethod
+    def get(cls):
+        if cls._fn is None:
+            torch = _torch()
+
+            class _Overlap(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, psi, u, lattice, n, rho, am, tol, prec):
+                    lattice.build_links(u.detach().contiguous(), 0.0)
+                    y, _ = lattice.overlap_apply(psi.detach().contiguous(), n, rho=rho, am=am, tol=tol, prec=prec)
+                    ctx.save_for_backward(psi.detach())
+                    ctx.cfg = (lattice, n, rho, am, tol, prec)
+                    return y
+
+                @staticmethod
+                def backward(ctx, grad_y):
+                    (psi,) = ctx.saved_tensors
+                    lattice, n, rho, am, tol, prec = ctx.cfg
+                    g_psi, g_u, _ = lattice.overlap_grad(grad_y.contiguous(), psi, n, rho=rho, am=am, tol=tol,
+                                                         prec=prec)
+                    return g_psi, g_u, None, None, None, None, None, None
+
+            cls._fn = _Overlap
+        return cls._fn
+
+
+def overlap(psi, u, lattice, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64):
+    """Differentiable D_m psi = (1 - am/(2 rho)) D_ov psi + am psi (links rebuilt from ``u``, c_sw = 0)."""
+    return OverlapFunction.get().apply(psi, u, lattice, n, rho, am, tol, prec)

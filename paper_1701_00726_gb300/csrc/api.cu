@@ -2,6 +2,7 @@
 // coefficients.
 #include "internal.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -290,6 +291,61 @@ int overlap_apply(bri_ctx* c, void* y, const void* x, int nrhs, int n, int kind,
   // (1 - am/(2 rho)) rho (x + s) + am x
   const double k = (1.0 - am / (2.0 * rho)) * rho;
   return sign_apply(c, (double2*)y, (const double2*)x, nrhs, n, kind, rho, scale, tol, prec, k, k + am, st);
+}
+
+int overlap_grad(bri_ctx* c, void* g_psi, void* g_U, const void* eta, const void* psi, int nrhs, int n, int kind,
+                 double rho, double am, double scale, double tol, int prec, bri_stats* st) {
+  int rc = check_solver(c, g_psi, psi, nrhs, n, rho, tol, prec, "overlap_grad");
+  if (rc) return rc;
+  if (!g_U || !eta || eta == g_psi || ((uintptr_t)eta & 15) || ((uintptr_t)g_U & 15)) {
+    set_error("overlap_grad: null, aliased or misaligned eta / g_U");
+    return BRI_ERR_INVALID;
+  }
+  if (c->have_clover) {
+    set_error("overlap_grad: the clover term is not differentiated; build the links with c_sw = 0");
+    return BRI_ERR_INVALID;
+  }
+  if (!std::isfinite(am) || am >= 2.0 * rho) {
+    set_error("overlap_grad: the traditional massive form needs am < 2 rho");
+    return BRI_ERR_INVALID;
+  }
+  return overlap_grad_impl(c, (double*)g_psi, (double*)g_U, (const double*)eta, (const double*)psi, nrhs, n, kind,
+                           rho, am, scale, tol, prec, st);
+}
+
+int overlap_solve(bri_ctx* c, void* x, const void* b, int nrhs, int n_outer, int n_inner, int kind, double rho,
+                  double am, int complete, double tol, int prec, bri_stats* st) {
+  int rc = check_solver(c, x, b, nrhs, n_outer, rho, tol, prec, "overlap_solve");
+  if (rc) return rc;
+  if (n_inner < 0 || n_inner > BRI_MAX_SHIFTS || !std::isfinite(am) || am < 0.0 || am >= 2.0 * rho) {
+    set_error("overlap_solve: need 0 <= n_inner <= 32 and 0 <= am < 2 rho");
+    return BRI_ERR_INVALID;
+  }
+  const int64_t nc = c->g.V * 12;
+  const int maxiter = (st && st->maxiter > 0) ? st->maxiter : 1000;
+  int worst = BRI_OK;
+  bri_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  for (int r = 0; r < nrhs; ++r) {
+    bri_stats one;
+    memset(&one, 0, sizeof(one));
+    rc = overlap_solve_impl(c, (double2*)x + r * nc, (const double2*)b + r * nc, n_outer, n_inner, kind, rho, am,
+                            complete, tol, prec, maxiter, &one);
+    if (rc < 0) return rc;
+    worst = std::max(worst, rc);
+    acc.iterations = std::max(acc.iterations, one.iterations);
+    acc.refinements += one.refinements;
+    acc.matvecs += one.matvecs;
+    acc.max_true_residual = std::max(acc.max_true_residual, one.max_true_residual);
+  }
+  if (st) {
+    const int want = st->want_true_residual, mi = st->maxiter;
+    *st = acc;
+    st->n_shifts = n_outer;
+    st->want_true_residual = want;
+    st->maxiter = mi;
+  }
+  return worst;
 }
 
 int bri_profile_enable(bri_ctx* c, int enable) {

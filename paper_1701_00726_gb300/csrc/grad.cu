@@ -1,0 +1,376 @@
+// Adjoint of the overlap application: gradients of
+//   L = sum_r Re <eta_r, D_m psi_r>,  D_m = (1 - am/(2 rho)) D_ov + am,
+//   D_ov = rho (1 + D r(D^dagger D)),  r(s) = c0 + sum_i w_i/(s + sigma_i)
+// with respect to the sources psi and the thin links U given to
+// bri_build_links (real-gradient convention dL = Re<g, dpsi> and
+// dL = Re sum tr(G^dagger dU)).  With k = (1 - am/(2 rho)) rho,
+// x_i = (A + sigma_i)^{-1} psi, z_i = (A + sigma_i)^{-1} D^dagger eta and
+// y = c0 psi + sum_i w_i x_i (both multi-shift solves share the shifts):
+//   g_psi = D_m^dagger eta = gamma5 D_m gamma5 eta,
+//   dL = k Re<eta, dD y> - k sum_i w_i (Re<D x_i, dD z_i> + Re<D z_i, dD x_i>).
+// Each term Re<u, dD v> gives every transporter W_d(n) the gradient
+// G_W = u(n) (M_d v(n+d))^dagger (kernel k_force); the gradients are then
+// pushed back through the path average (App. C) by reversing the last-step
+// recursion W_d = (1/k) sum_mu W_{d - s e_mu} U_step level by level, as
+// gathers (no atomics).  The clover term is not differentiated (c_SW = 0).
+#include "bri_kernel.cuh"
+
+namespace bri {
+namespace {
+
+// out = gamma5 in (spins 2 and 3 negated), FP64 spinors
+__global__ void k_gamma5(int64_t nsite_rhs, const double2* __restrict__ in, double2* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsite_rhs * 12;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int spin = (int)((i % 12) / 3);
+    double2 v = in[i];
+    if (spin >= 2) {
+      v.x = -v.x;
+      v.y = -v.y;
+    }
+    out[i] = v;
+  }
+}
+
+struct PairList {
+  const double* u[512];
+  const double* v[512];
+  double w[512];
+};
+
+// G_W[idx](n) += sum_p w_p u_p(n) (M_d v_p(n+d))^dagger for the 80 hops d.
+// blockIdx.y = stored offset j (0..39), blockIdx.z = 0 for +d, 1 for -d.
+__global__ void __launch_bounds__(128) k_force(Geom g, const PairList* __restrict__ pl, int npair, double2* GW) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.V) return;
+  const int j = blockIdx.y, opp = blockIdx.z;
+  const HopTable<double>& H = c_hops_d;
+  int m = 0;
+  {
+    int r = n;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int L = g.L[mu];
+      const int cmu = (mu < 3) ? r % L : r;
+      if (mu < 3) r /= L;
+      const int d = opp ? -H.site_d[j][mu] : H.site_d[j][mu];
+      m += wrap(cmu + d, L) * (int)g.str[mu];
+    }
+  }
+  const double a = H.a[j];
+  const double sg = opp ? -1.0 : 1.0;
+  const double c1 = sg * H.cs[j][0], c2 = sg * H.cs[j][1], c3 = sg * H.cs[j][2], c4 = sg * H.cs[j][3];
+  C<double> G[3][3];
+#pragma unroll
+  for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) G[aa][b] = C<double>{0, 0};
+  for (int p = 0; p < npair; ++p) {
+    Spinor<double> us, vs, chi;
+    load_spinor(us, pl->u[p] + (int64_t)n * 24);
+    load_spinor(vs, pl->v[p] + (int64_t)m * 24);
+    spin_combine(chi, vs, a, c1, c2, c3, c4);
+    const double wp = pl->w[p];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        const C<double> ua{wp * us.v[s][aa].re, wp * us.v[s][aa].im};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) cfma_cj(G[aa][b], chi.v[s][b], ua);  // u_a conj(chi_b)
+      }
+  }
+  const int idx = opp ? 80 - j : j;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    double2* q = GW + ((int64_t)idx * 9 + e) * g.V + n;
+    double2 v = *q;
+    v.x += G[e / 3][e % 3].re;
+    v.y += G[e / 3][e % 3].im;
+    *q = v;
+  }
+}
+
+__device__ __forceinline__ int site_shift(const Geom& g, int n, const int d[4]) {
+  int r = n, m = 0;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = g.L[mu];
+    const int cmu = (mu < 3) ? r % L : r;
+    if (mu < 3) r /= L;
+    int v = (cmu + d[mu]) % L;
+    if (v < 0) v += L;
+    m += v * (int)g.str[mu];
+  }
+  return m;
+}
+
+__device__ __forceinline__ M3<double> ldm(const double2* base, int64_t V, int64_t n) {
+  M3<double> m;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const double2 v = base[(int64_t)e * V + n];
+    m.m[e / 3][e % 3] = C<double>{v.x, v.y};
+  }
+  return m;
+}
+
+__device__ __forceinline__ void addm(double2* base, int64_t V, int64_t n, const M3<double>& a, double s) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    double2* q = base + (int64_t)e * V + n;
+    double2 v = *q;
+    v.x += s * a.m[e / 3][e % 3].re;
+    v.y += s * a.m[e / 3][e % 3].im;
+    *q = v;
+  }
+}
+
+__device__ __forceinline__ int nu_idx(const int d[4]) {
+  return (d[0] + 1) + 3 * (d[1] + 1) + 9 * (d[2] + 1) + 27 * (d[3] + 1);
+}
+
+// Level-k link gradients (gather over the transporters whose last hop is U_mu(m)):
+//   forward hop  W_d(n) = ... W_{d'}(n) U_mu(n + d'):        G_U_mu(m) += (1/k) W_{d'}(n)^dagger G_W[d](n), n = m - d'
+//   backward hop W_d(n) = ... W_{d'}(n) U_mu(n + d' - mu)^+: G_U_mu(m) += (1/k) G_W[d](n)^dagger W_{d'}(n), n = m - d' + mu
+__global__ void k_rev_links(Geom g, LevelList lst, int k, const double2* __restrict__ T,
+                            const double2* __restrict__ GW, double2* GU) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.y;
+  if (m >= g.V) return;
+  M3<double> acc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc.m[a][b] = C<double>{0, 0};
+  for (int i = 0; i < lst.count; ++i) {
+    const int nu = lst.nu[i];
+    int d[4] = {nu % 3 - 1, (nu / 3) % 3 - 1, (nu / 9) % 3 - 1, (nu / 27) % 3 - 1};
+    const int s = d[mu];
+    if (s == 0) continue;
+    int dp[4] = {d[0], d[1], d[2], d[3]};
+    dp[mu] -= s;
+    int back[4] = {-dp[0], -dp[1], -dp[2], -dp[3]};
+    if (s < 0) back[mu] += 1;
+    const int n = site_shift(g, m, back);
+    const M3<double> gw = ldm(GW + (int64_t)nu * 9 * g.V, g.V, n);
+    const M3<double> wp = ldm(T + (int64_t)nu_idx(dp) * 9 * g.V, g.V, n);
+    madd(acc, s > 0 ? mmul(adj(wp), gw) : mmul(adj(gw), wp));
+  }
+  addm(GU + (int64_t)mu * 9 * g.V, g.V, m, acc, 1.0 / k);
+}
+
+// Level-k transporter gradients passed down to level k-1 (same site):
+//   G_W[d'](n) += (1/k) sum_{mu: d'_mu = 0, s = +-1} G_W[d' + s e_mu](n) S^dagger,
+//   S = U_mu(n + d') (s = +1) or U_mu(n + d' - mu)^dagger (s = -1).
+__global__ void k_rev_transporters(Geom g, LevelList lower, int k, const double2* __restrict__ U64, double2* GW) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int which = blockIdx.y;
+  if (n >= g.V || which >= lower.count) return;
+  const int nup = lower.nu[which];
+  const int dp[4] = {nup % 3 - 1, (nup / 3) % 3 - 1, (nup / 9) % 3 - 1, (nup / 27) % 3 - 1};
+  M3<double> acc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc.m[a][b] = C<double>{0, 0};
+  for (int mu = 0; mu < 4; ++mu) {
+    if (dp[mu] != 0) continue;
+    for (int s = -1; s <= 1; s += 2) {
+      int d[4] = {dp[0], dp[1], dp[2], dp[3]};
+      d[mu] = s;
+      const M3<double> gw = ldm(GW + (int64_t)nu_idx(d) * 9 * g.V, g.V, n);
+      int at[4] = {dp[0], dp[1], dp[2], dp[3]};
+      if (s < 0) at[mu] -= 1;
+      const int ms = site_shift(g, n, at);
+      const M3<double> u = ldm(U64 + (int64_t)mu * 9 * g.V, g.V, ms);
+      madd(acc, s > 0 ? mmul(gw, adj(u)) : mmul(gw, u));
+    }
+  }
+  addm(GW + (int64_t)nup * 9 * g.V, g.V, n, acc, 1.0 / k);
+}
+
+// One-hop transporters: W_{+mu}(m) = U_mu(m), W_{-mu}(m + mu) = U_mu(m)^dagger.
+__global__ void k_rev_level1(Geom g, const double2* __restrict__ GW, double2* GU) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.y;
+  if (m >= g.V) return;
+  int e[4] = {0, 0, 0, 0};
+  e[mu] = 1;
+  const int fwd = nu_idx(e);
+  int ne[4] = {-e[0], -e[1], -e[2], -e[3]};
+  const int bwd = nu_idx(ne);
+  const int mp = site_shift(g, m, e);
+  M3<double> acc = ldm(GW + (int64_t)fwd * 9 * g.V, g.V, m);
+  madd(acc, adj(ldm(GW + (int64_t)bwd * 9 * g.V, g.V, mp)));
+  addm(GU + (int64_t)mu * 9 * g.V, g.V, m, acc, 1.0);
+}
+
+// SoA [4][9][V] -> caller layout [V][4][3][3], with the antiperiodic sign of
+// U_t on the last time slice carried back to the original links.
+__global__ void k_links_out(Geom g, const double2* __restrict__ GU, double2* out, int anti) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.V) return;
+  const int t = (int)(n / g.str[3]);
+  for (int mu = 0; mu < 4; ++mu) {
+    const double sg = (anti && mu == 3 && t == g.L[3] - 1) ? -1.0 : 1.0;
+    for (int e = 0; e < 9; ++e) {
+      double2 v = GU[((int64_t)mu * 9 + e) * g.V + n];
+      out[((int64_t)n * 4 + mu) * 9 + e] = make_double2(sg * v.x, sg * v.y);
+    }
+  }
+}
+
+__global__ void k_zero(int64_t n, double2* p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_double2(0.0, 0.0);
+}
+
+struct Buf {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  ~Buf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  int alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      set_error(std::string("cudaMallocAsync failed: ") + cudaGetErrorString(e));
+      return BRI_ERR_OOM;
+    }
+    return BRI_OK;
+  }
+  template <typename T> T* as() const { return (T*)p; }
+};
+
+// acc = c0 b + sum_i w_i X_i for systems s < nout of an X with nsys systems per shift
+__global__ void k_rational_sub(int64_t nreal, int nsys, int nshift, double c0, const double* __restrict__ w,
+                               const double* __restrict__ b, const double* __restrict__ X, double* out) {
+  const int s = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nreal; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = c0 * b[s * nreal + i];
+    for (int k = 0; k < nshift; ++k) v += w[k] * X[((int64_t)k * nsys + s) * nreal + i];
+    out[s * nreal + i] = v;
+  }
+}
+
+}  // namespace
+
+int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta, const double* psi, int nrhs, int n,
+                      int kind, double rho, double am, double scale, double tol, int prec, bri_stats* stats) {
+  cudaStream_t st = c->stream;
+  const Geom& g = c->g;
+  const int64_t V = g.V, nreal = V * 24;
+  const double m0 = -rho;
+  double c0, w[BRI_MAX_SHIFTS], sig[BRI_MAX_SHIFTS];
+  int rc = kl_host(n, kind, scale, &c0, w, sig);
+  if (rc) return rc;
+  if ((rc = ensure_hops())) return rc;
+  const double kfac = (1.0 - am / (2.0 * rho)) * rho;
+
+  // g_psi = gamma5 D_m gamma5 eta
+  Buf bg5;
+  if ((rc = bg5.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  k_gamma5<<<1024, 256, 0, st>>>(V * nrhs, (const double2*)eta, bg5.as<double2>()); note_launch();
+  bri_stats st_ov;
+  memset(&st_ov, 0, sizeof(st_ov));
+  if (stats) st_ov.maxiter = stats->maxiter;
+  rc = sign_apply(c, (double2*)g_psi, bg5.as<double2>(), nrhs, n, kind, rho, scale, tol, prec, kfac, kfac + am, &st_ov);
+  if (rc < 0) return rc;
+  int solve_rc = rc;
+  k_gamma5<<<1024, 256, 0, st>>>(V * nrhs, (const double2*)g_psi, (double2*)g_psi); note_launch();
+
+  // shifted solves for psi and D^dagger eta (2 nrhs systems, same shifts)
+  const int nsys = 2 * nrhs;
+  Buf bb, bX, bDX, by;
+  if ((rc = bb.alloc(sizeof(double) * nreal * nsys, st))) return rc;
+  BRI_CUDA(cudaMemcpyAsync(bb.as<double>(), psi, sizeof(double) * nreal * nrhs, cudaMemcpyDeviceToDevice, st));
+  if ((rc = dirac_bri(c, bb.as<double>() + nreal * nrhs, eta, nrhs, m0, 1, BRI_PREC_F64, st))) return rc;
+  std::vector<double> sig_all((size_t)nsys * n);
+  for (int s = 0; s < nsys; ++s)
+    for (int k = 0; k < n; ++k) sig_all[(size_t)s * n + k] = sig[k];
+  if ((rc = bX.alloc(sizeof(double) * nreal * nsys * n, st))) return rc;
+  SolveInfo info;
+  const int maxiter = (stats && stats->maxiter > 0) ? stats->maxiter : 20000;
+  rc = solve_shifts(c, bb.as<double>(), nsys, n, sig_all.data(), m0, tol, prec, maxiter, bX.as<double>(), info);
+  if (rc < 0) return rc;
+  if (rc > solve_rc) solve_rc = rc;
+  double* X = bX.as<double>();
+
+  // y = c0 psi + sum w_i x_i ; D X for every shift and system
+  Buf bw;
+  if ((rc = bw.alloc(sizeof(double) * BRI_MAX_SHIFTS, st))) return rc;
+  BRI_CUDA(cudaMemcpyAsync(bw.as<double>(), w, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  if ((rc = by.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  k_rational_sub<<<dim3(256, nrhs), 256, 0, st>>>(nreal, nsys, n, c0, bw.as<double>(), psi, X, by.as<double>());
+  note_launch();
+  if ((rc = bDX.alloc(sizeof(double) * nreal * nsys * n, st))) return rc;
+  if ((rc = dirac_bri(c, bDX.as<double>(), X, nsys * n, m0, 0, BRI_PREC_F64, st))) return rc;
+  BRI_LAUNCH_CHECK("overlap_grad solves");
+
+  // transporter gradients from all (u, v, weight) pairs
+  Buf bGW, bpl;
+  if ((rc = bGW.alloc(sizeof(double2) * 81 * 9 * V, st))) return rc;
+  k_zero<<<2048, 256, 0, st>>>(81 * 9 * V, bGW.as<double2>()); note_launch();
+  if ((rc = bpl.alloc(sizeof(PairList), st))) return rc;
+  const int per_rhs = 1 + 2 * n;
+  const int rhs_per_chunk = std::max(1, 512 / per_rhs);
+  std::vector<PairList> hpl((nrhs + rhs_per_chunk - 1) / rhs_per_chunk);
+  for (int r0 = 0, ci = 0; r0 < nrhs; r0 += rhs_per_chunk, ++ci) {
+    PairList& pl = hpl[ci];
+    int np = 0;
+    for (int r = r0; r < std::min(nrhs, r0 + rhs_per_chunk); ++r) {
+      pl.u[np] = eta + r * nreal;
+      pl.v[np] = by.as<double>() + r * nreal;
+      pl.w[np++] = kfac;
+      for (int i = 0; i < n; ++i) {
+        const double* xi = X + ((int64_t)i * nsys + r) * nreal;
+        const double* zi = X + ((int64_t)i * nsys + nrhs + r) * nreal;
+        const double* dxi = bDX.as<double>() + ((int64_t)i * nsys + r) * nreal;
+        const double* dzi = bDX.as<double>() + ((int64_t)i * nsys + nrhs + r) * nreal;
+        pl.u[np] = dxi;
+        pl.v[np] = zi;
+        pl.w[np++] = -kfac * w[i];
+        pl.u[np] = dzi;
+        pl.v[np] = xi;
+        pl.w[np++] = -kfac * w[i];
+      }
+    }
+    BRI_CUDA(cudaMemcpyAsync(bpl.as<PairList>(), &pl, sizeof(PairList), cudaMemcpyHostToDevice, st));
+    dim3 grid(blocks_for(V, 128), 40, 2);
+    k_force<<<grid, 128, 0, st>>>(g, bpl.as<PairList>(), np, bGW.as<double2>()); note_launch();
+    BRI_CUDA(cudaStreamSynchronize(st));  // the pair list buffer is reused
+  }
+
+  // back through the path average to the thin links
+  Buf bT, bGU;
+  if ((rc = bT.alloc(sizeof(double2) * 81 * 9 * V, st))) return rc;
+  if ((rc = build_transporters(c, bT.as<double2>()))) return rc;
+  if ((rc = bGU.alloc(sizeof(double2) * 36 * V, st))) return rc;
+  k_zero<<<512, 256, 0, st>>>(36 * V, bGU.as<double2>()); note_launch();
+  for (int k = 4; k >= 2; --k) {
+    const LevelList lst = level_list(k), lower = level_list(k - 1);
+    k_rev_links<<<dim3(blocks_for(V, 128), 4), 128, 0, st>>>(g, lst, k, bT.as<double2>(), bGW.as<double2>(),
+                                                            bGU.as<double2>()); note_launch();
+    k_rev_transporters<<<dim3(blocks_for(V, 128), lower.count), 128, 0, st>>>(g, lower, k, c->U64,
+                                                                             bGW.as<double2>()); note_launch();
+  }
+  k_rev_level1<<<dim3(blocks_for(V, 128), 4), 128, 0, st>>>(g, bGW.as<double2>(), bGU.as<double2>()); note_launch();
+  k_links_out<<<blocks_for(V, 128), 128, 0, st>>>(g, bGU.as<double2>(), (double2*)g_U,
+                                                  (c->flags & BRI_ANTIPERIODIC_T) ? 1 : 0); note_launch();
+  BRI_LAUNCH_CHECK("overlap_grad backward");
+  BRI_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->iterations = std::max(st_ov.iterations, info.iters);
+    stats->matvecs = st_ov.matvecs + info.cnt.matvecs + 3;
+    stats->matvecs_f64 = st_ov.matvecs_f64 + info.cnt.matvecs64 + 3;
+    stats->refinements = st_ov.refinements + info.refinements;
+    stats->n_shifts = n;
+  }
+  return solve_rc;
+}
+
+}  // namespace bri

@@ -89,7 +89,15 @@ struct bri_ctx {
 namespace bri {
 
 // ---------------------------------------------------------------- kernels (host launchers)
+// Offsets (nu - 1) with exactly k nonzero components.
+struct LevelList {
+  int count;
+  int nu[32];
+};
+LevelList level_list(int k);
 int launch_build_links(bri_ctx* c, const double* U, double c_sw);
+// All 81 path-averaged transporters [81][9][V] (FP64) from the thin links of the context.
+int build_transporters(bri_ctx* c, double2* T);
 int launch_export_links(bri_ctx* c, double* W);
 
 // spinor precision dispatch for the stencils
@@ -113,6 +121,21 @@ ScratchArena* current_arena();
 int kl_host(int n, int kind, double scale, double* c0, double* w, double* sigma);
 
 // solvers
+struct Counters {
+  int matvecs = 0, matvecs64 = 0;
+};
+struct SolveInfo {
+  Counters cnt;
+  int iters = 0, refinements = 0;
+  double tph[4] = {0, 0, 0, 0};
+};
+// (A + sigma_k) X_k = b_s for all shifts k < n, systems s < nsys: X = [n][nsys][V*24] FP64.
+int solve_shifts(bri_ctx* c, const double* b, int nsys, int n, const double* sig, double m0, double tol, int prec,
+                 int maxiter, double* X, SolveInfo& info);
+int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta, const double* psi, int nrhs, int n,
+                      int kind, double rho, double am, double scale, double tol, int prec, bri_stats* stats);
+int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, int n_inner, int kind, double rho,
+                       double am, int complete, double tol, int prec, int maxiter, bri_stats* st_out);
 int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho,
                double scale, double tol, int prec, double out_scale, double b_coeff,
                bri_stats* st);

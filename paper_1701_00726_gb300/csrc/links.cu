@@ -94,10 +94,20 @@ __global__ void level1_kernel(Geom g, const double2* __restrict__ U64, double2* 
   }
 }
 
-struct LevelList {
-  int count;
-  int nu[32];
-};
+}  // namespace
+
+LevelList level_list(int k) {
+  LevelList lst;
+  lst.count = 0;
+  for (int nu = 0; nu < 81; ++nu) {
+    int d[4] = {nu % 3 - 1, (nu / 3) % 3 - 1, (nu / 9) % 3 - 1, (nu / 27) % 3 - 1};
+    int h = (d[0] != 0) + (d[1] != 0) + (d[2] != 0) + (d[3] != 0);
+    if (h == k) lst.nu[lst.count++] = nu;
+  }
+  return lst;
+}
+
+namespace {
 
 // k-hop transporters from (k-1)-hop ones at the same site (last-step recursion).
 __global__ void levelk_kernel(Geom g, const double2* __restrict__ U64, double2* T, LevelList lst, int k) {
@@ -245,6 +255,21 @@ __global__ void export_links_kernel(Geom g, const double2* __restrict__ W64, dou
 
 }  // namespace
 
+int build_transporters(bri_ctx* c, double2* T) {
+  const Geom& g = c->g;
+  const int64_t V = g.V;
+  cudaStream_t st = c->stream;
+  const int th = 128;
+  level1_kernel<<<blocks_for(V, th), th, 0, st>>>(g, c->U64, T); note_launch();
+  for (int k = 2; k <= 4; ++k) {
+    LevelList lst = level_list(k);
+    dim3 grid(blocks_for(V, th), lst.count);
+    levelk_kernel<<<grid, th, 0, st>>>(g, c->U64, T, lst, k); note_launch();
+  }
+  BRI_LAUNCH_CHECK("link construction kernels");
+  return BRI_OK;
+}
+
 int launch_build_links(bri_ctx* c, const double* U, double c_sw) {
   const Geom& g = c->g;
   const int64_t V = g.V;
@@ -271,19 +296,7 @@ int launch_build_links(bri_ctx* c, const double* U, double c_sw) {
   const int th = 128;
   thin_links_kernel<<<blocks_for(V, th), th, 0, st>>>(g, (const double2*)U, c->U64, c->U32,
                                                        (c->flags & BRI_ANTIPERIODIC_T) ? 1 : 0); note_launch();
-  level1_kernel<<<blocks_for(V, th), th, 0, st>>>(g, c->U64, T); note_launch();
-  for (int k = 2; k <= 4; ++k) {
-    LevelList lst;
-    lst.count = 0;
-    for (int nu = 0; nu < 81; ++nu) {
-      int d[4] = {nu % 3 - 1, (nu / 3) % 3 - 1, (nu / 9) % 3 - 1, (nu / 27) % 3 - 1};
-      int h = (d[0] != 0) + (d[1] != 0) + (d[2] != 0) + (d[3] != 0);
-      if (h == k) lst.nu[lst.count++] = nu;
-    }
-    dim3 grid(blocks_for(V, th), lst.count);
-    levelk_kernel<<<grid, th, 0, st>>>(g, c->U64, T, lst, k); note_launch();
-  }
-  BRI_LAUNCH_CHECK("link construction kernels");
+  if ((rc = build_transporters(c, T))) return rc;
   BRI_CUDA(cudaMemcpyAsync(c->W64, T, sizeof(double2) * 360 * V, cudaMemcpyDeviceToDevice, st));
   narrow_links_kernel<<<blocks_for(360 * V, 256), 256, 0, st>>>(360 * V, c->W64, c->W32, c->W16); note_launch();
   BRI_LAUNCH_CHECK("narrow_links_kernel");

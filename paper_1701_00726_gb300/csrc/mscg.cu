@@ -314,12 +314,6 @@ __global__ void k_convert(int64_t n, const A* __restrict__ in, B* out) {
     out[i] = (B)in[i];
 }
 
-// X (FP64) += (double) e (FP32), n reals
-__global__ void k_accumulate(int64_t n, double* X, const float* __restrict__ e) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    X[i] += (double)e[i];
-}
-
 // res = b - q - sigma X ; partial ||res||^2 ; q is (A X)
 __global__ void k_residual(int64_t n, const double* __restrict__ b, const double* __restrict__ q,
                            const double* __restrict__ X, double sigma, double* res, double* part) {
@@ -438,9 +432,6 @@ template <typename R> int op_prec(int prec);
 template <> int op_prec<double>(int) { return BRI_PREC_F64; }
 template <> int op_prec<float>(int prec) { return prec == BRI_PREC_F32_BF16 ? BRI_PREC_F32_BF16 : BRI_PREC_F32; }
 
-struct Counters {
-  int matvecs = 0, matvecs64 = 0;
-};
 
 // Solve (A + sig[s][k]) x[k][s] = b[s] for nsys systems with nshift shifts each.
 // sig: host [nsys][nshift], increasing within a system.
@@ -558,26 +549,21 @@ int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X
 
 }  // namespace
 
-int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho, double scale,
-               double tol, int prec, double out_scale, double b_coeff, bri_stats* stats) {
-  auto t0 = std::chrono::steady_clock::now();
-  configure_pool_once();
+// Solve (A + sigma_k) X_k = b_s for every shift k < n and system s < nsys,
+// X = [n][nsys][V*24] FP64; FP64 multi-shift CG or the mixed scheme above.
+
+int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig, double m0, double tol,
+                 int prec, int maxiter, double* X, SolveInfo& info) {
   cudaStream_t st = c->stream;
   const int64_t nreal = c->g.V * 24;
-  const double m0 = -rho;
-  double c0, w[NS], sig[NS];
-  int rc = kl_host(n, kind, scale, &c0, w, sig);
-  if (rc) return rc;
-  const int maxiter = (stats && stats->maxiter > 0) ? stats->maxiter : 20000;
-  Counters cnt;
-  int iters = 0, refinements = 0;
-  const double* b = (const double*)x;
-
+  int rc = BRI_OK;
+  Counters& cnt = info.cnt;
+  int& iters = info.iters;
+  int& refinements = info.refinements;
   std::vector<double> sig_all((size_t)nrhs * n);
   for (int s = 0; s < nrhs; ++s)
     for (int k = 0; k < n; ++k) sig_all[(size_t)s * n + k] = sig[k];
 
-  double tph[4] = {0, 0, 0, 0};
   auto tnow = [&]() {
     cudaStreamSynchronize(st);
     return std::chrono::steady_clock::now();
@@ -585,14 +571,10 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   auto tmark = tnow();
   auto lap = [&](int ph) {
     auto t1 = tnow();
-    tph[ph] += std::chrono::duration<double>(t1 - tmark).count();
+    info.tph[ph] += std::chrono::duration<double>(t1 - tmark).count();
     tmark = t1;
   };
-  DevBuf bX;
-  if ((rc = bX.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
-  double* X = bX.as<double>();
   int solve_rc = BRI_OK;
-
   if (prec == BRI_PREC_F64) {
     solve_rc = multishift_solve<double>(c, prec, m0, nrhs, n, sig_all.data(), b, X, tol, maxiter, &iters, &cnt,
                                         nullptr);
@@ -738,6 +720,33 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
     return BRI_ERR_INVALID;
   }
 
+  return solve_rc;
+}
+
+int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho, double scale,
+               double tol, int prec, double out_scale, double b_coeff, bri_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  configure_pool_once();
+  cudaStream_t st = c->stream;
+  const int64_t nreal = c->g.V * 24;
+  const double m0 = -rho;
+  double c0, w[NS], sig[NS];
+  int rc = kl_host(n, kind, scale, &c0, w, sig);
+  if (rc) return rc;
+  const int maxiter = (stats && stats->maxiter > 0) ? stats->maxiter : 20000;
+  const double* b = (const double*)x;
+
+  double tph[4] = {0, 0, 0, 0};
+  DevBuf bX;
+  if ((rc = bX.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
+  double* X = bX.as<double>();
+  SolveInfo info;
+  int solve_rc = solve_shifts(c, b, nrhs, n, sig, m0, tol, prec, maxiter, X, info);
+  if (solve_rc < 0) return solve_rc;
+  Counters& cnt = info.cnt;
+  const int iters = info.iters, refinements = info.refinements;
+  for (int ph = 0; ph < 3; ++ph) tph[ph] = info.tph[ph];
+  auto tmark = std::chrono::steady_clock::now();
   // optional FP64 true residuals for the statistics
   if (stats && stats->want_true_residual) {
     DevBuf btmp1, btmp2, bpart, bdsum;
@@ -777,9 +786,9 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   cnt.matvecs += 1;
   cnt.matvecs64 += 1;
   k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), (double*)y); note_launch();
-  lap(3);
   BRI_LAUNCH_CHECK("k_axpby");
   BRI_CUDA(cudaStreamSynchronize(st));
+  tph[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tmark).count();
   if (stats) {
     stats->iterations = iters;
     stats->matvecs = cnt.matvecs;
