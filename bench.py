@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--stencil-probe", default=None, metavar="LX,LY,LZ,LT",
                     help="profiling helper: only launch the FP32 Brillouin stencil on this lattice and print "
                          "its CUDA-event time (used for the ncu captures under profiles/)")
+    ap.add_argument("--batch-c4", action="store_true",
+                    help="time the batched workload instead: 12 point sources on 16^3x32 plus 8 uneven lattices, "
+                         "KL order 12, mixed precision, one concurrent batch vs lattice after lattice")
     ap.add_argument("--probe-nrhs", type=int, default=1)
     ap.add_argument("--probe-launches", type=int, default=4)
     return ap.parse_args()
@@ -227,8 +230,45 @@ def run_reference(args):
     }), flush=True)
 
 
+def batch_c4(args):
+    import torch
+
+    import synthetic_fields as sf
+    from paper_1701_00726_gb300 import PREC_F32, Lattice, overlap_apply_batch
+    shapes = [(16, 16, 16, 32), (8, 8, 8, 8), (8, 8, 8, 16), (12, 12, 12, 24), (16, 16, 16, 16), (12, 12, 12, 12),
+              (12, 12, 12, 12), (8, 8, 8, 24), (8, 8, 8, 24)]
+    lats, xs = [], []
+    for i, dims in enumerate(shapes):
+        lat = Lattice(dims)
+        lat.build_links(torch.from_numpy(sf.gauge_field(dims, 10 + i, 0.1, 3, device="cuda")).cuda(), C_SW)
+        lats.append(lat)
+        src = sf.point_sources(dims) if i == 0 else sf.gaussian_source(dims, 1, 1010 + i)
+        xs.append(torch.from_numpy(src).cuda())
+    applies = sum(x.shape[0] for x in xs)
+    for _ in range(max(1, args.warmup)):
+        overlap_apply_batch(lats, xs, n=12, tol=TOL, prec=PREC_F32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        overlap_apply_batch(lats, xs, n=12, tol=TOL, prec=PREC_F32)
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / args.steps
+    t0 = time.perf_counter()
+    for lat, x in zip(lats, xs):
+        lat.overlap_apply(x, n=12, tol=TOL, prec=PREC_F32)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    print(json.dumps({"workload": "batched overlap: 12 point sources on 16^3x32 + 8 lattices (8^4, 8^3x16, "
+                                  "12^3x24, 16^4, 2x12^4, 2x8^3x24), KL order 12, mixed, tol 1e-10",
+                      "applies_per_step": applies, "batch_s_per_step": tb, "sequential_s_per_step": ts,
+                      "batch_applies_per_s": applies / tb, "speedup_vs_sequential": ts / tb}), flush=True)
+
+
 def main():
     args = parse()
+    if args.batch_c4:
+        batch_c4(args)
+        return
     if args.stencil_probe:
         stencil_probe(args)
         return

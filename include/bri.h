@@ -134,6 +134,20 @@ int sign_apply_multishift(bri_ctx* ctx, void* y, const void* x, int nrhs, int n,
 int overlap_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
                   double rho, double am, double scale, double tol, int prec, bri_stats* st);
 
+/* Batched overlap application over several independent lattices (e.g. gauge
+ * fields of uneven volume): the same as calling overlap_apply on each context,
+ * but all lattices progress concurrently, each on its context's own stream
+ * driven by its own host thread, so that small lattices share the GPU.
+ * Solver iterations after the first block are replayed from CUDA graphs
+ * captured once per active-system count (disabled with BRI_GRAPHS=0 or while
+ * the context is profiling); the stencil launch configuration is autotuned per
+ * lattice shape and right-hand-side count on first use (BRI_AUTOTUNE=0
+ * disables it).  ctxs: nctx distinct contexts on the current device; ys[i],
+ * xs[i]: device complex128 [nrhs[i]][V_i][4][3]; st: NULL or an array of nctx
+ * statistics.  Returns the worst per-lattice code. */
+int overlap_apply_batch(bri_ctx* const* ctxs, int nctx, void* const* ys, const void* const* xs, const int* nrhs,
+                        int n, int kind, double rho, double am, double scale, double tol, int prec, bri_stats* st);
+
 /* Massive overlap solve D_m x = b (Secs. 4.2-4.4) with cascaded
  * preconditioning (Sec. 8, Eqs. cascaded_one, cascaded_two): solves
  * (D_ov + mt) x = bt, mt = am/(1 - am/(2 rho)), with bt of the traditional

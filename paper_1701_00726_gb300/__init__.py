@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KL_DIAGONAL, KL_UPPER, PREC_F32, PREC_F32_BF16, PREC_F64,
                    BriError, BriStats, kl_coeffs)
 
-__all__ = ["Lattice", "overlap", "OverlapFunction", "kl_coeffs", "BriError", "BriStats", "PREC_F64", "PREC_F32", "PREC_F32_BF16",
+__all__ = ["Lattice", "overlap", "OverlapFunction", "overlap_apply_batch", "kl_coeffs", "BriError", "BriStats", "PREC_F64", "PREC_F32", "PREC_F32_BF16",
            "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T"]
 
 
@@ -212,6 +212,33 @@ class Lattice:
         d = st.as_dict()
         d["converged"] = rc == 0
         return y, d
+
+
+def overlap_apply_batch(lattices, xs, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL, scale=1.0):
+    """overlap_apply on several independent lattices at once (concurrently on the GPU).
+    Returns (list of y, list of stats)."""
+    torch = _torch()
+    k = len(lattices)
+    if k != len(xs) or k == 0:
+        raise BriError("need one source tensor per lattice")
+    lib = _lib.load()
+    nrhs = [lat._spinor(x, (torch.complex128,)) for lat, x in zip(lattices, xs)]
+    ys = [torch.empty_like(x) for x in xs]
+    for lat in lattices:  # the batch runs after everything already queued on the callers' streams
+        lat.stream.synchronize()
+    ctxs = (ctypes.c_void_p * k)(*[lat._h.value for lat in lattices])
+    yp = (ctypes.c_void_p * k)(*[y.data_ptr() for y in ys])
+    xp = (ctypes.c_void_p * k)(*[x.data_ptr() for x in xs])
+    nr = (ctypes.c_int * k)(*nrhs)
+    sts = (BriStats * k)()
+    rc = lib.overlap_apply_batch(ctxs, k, yp, xp, nr, int(n), int(kind), float(rho), float(am), float(scale),
+                                 float(tol), int(prec), sts)
+    _lib.check(rc, "overlap_apply_batch")
+    out = []
+    for i in range(k):
+        d = sts[i].as_dict()
+        out.append(d)
+    return ys, out
 
 
 class OverlapFunction:

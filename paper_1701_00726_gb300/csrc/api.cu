@@ -5,8 +5,11 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
+#include <vector>
 
 namespace bri {
 
@@ -14,6 +17,16 @@ static thread_local std::string g_err = "no error";
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int graphs_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("BRI_GRAPHS");
+    v = e ? (atoi(e) != 0) : 1;
+  }
+  return v && current_arena() == nullptr;
+}
 
 static cudaEvent_t pool_event(bri_ctx* c) {
   if (!c->prof_pool.empty()) {
@@ -170,6 +183,9 @@ void bri_destroy(bri_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->prof_pool) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   cudaFree(c->ws.ptr);
   cudaFree(c->ws_small.ptr);
   cudaFreeHost(c->host_pinned);
@@ -344,6 +360,46 @@ int overlap_solve(bri_ctx* c, void* x, const void* b, int nrhs, int n_outer, int
     st->n_shifts = n_outer;
     st->want_true_residual = want;
     st->maxiter = mi;
+  }
+  return worst;
+}
+
+int overlap_apply_batch(bri_ctx* const* ctxs, int nctx, void* const* ys, const void* const* xs, const int* nrhs,
+                        int n, int kind, double rho, double am, double scale, double tol, int prec, bri_stats* st) {
+  if (!ctxs || !ys || !xs || !nrhs || nctx < 1 || nctx > 256) {
+    set_error("overlap_apply_batch: need 1 <= nctx <= 256 and non-null arrays");
+    return BRI_ERR_INVALID;
+  }
+  for (int i = 0; i < nctx; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) {
+        set_error("overlap_apply_batch: a context appears twice");
+        return BRI_ERR_INVALID;
+      }
+    int rc = check_solver(ctxs[i], ys[i], xs[i], nrhs[i], n, rho, tol, prec, "overlap_apply_batch");
+    if (rc) return rc;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> rcs(nctx, BRI_OK);
+  std::vector<std::string> errs(nctx);
+  std::vector<std::thread> pool;
+  pool.reserve(nctx);
+  for (int i = 0; i < nctx; ++i) {
+    pool.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      rcs[i] = overlap_apply(ctxs[i], ys[i], xs[i], nrhs[i], n, kind, rho, am, scale, tol, prec, st ? &st[i] : nullptr);
+      if (rcs[i] < 0) errs[i] = bri_last_error();
+    });
+  }
+  for (auto& t : pool) t.join();
+  int worst = BRI_OK;
+  for (int i = 0; i < nctx; ++i) {
+    if (rcs[i] < 0) {
+      set_error("overlap_apply_batch: lattice " + std::to_string(i) + ": " + errs[i]);
+      return rcs[i];
+    }
+    worst = std::max(worst, rcs[i]);
   }
   return worst;
 }

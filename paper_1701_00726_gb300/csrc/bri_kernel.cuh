@@ -21,6 +21,9 @@
 
 #include "stencil.cuh"
 
+#include <cstdio>
+#include <vector>
+
 namespace bri {
 
 // Stored offsets nu = 1..40 with their identity weight -2^{-k-3} and the
@@ -190,29 +193,91 @@ __global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
 
 template <typename R, typename LS, int NR>
 inline void launch_bri_nr(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, R sgn, int rhs0,
-                          int groups, cudaStream_t s) {
-  const int th = 128;
-  dim3 grid(blocks_for(g.V, th), groups);
-  bri_kernel<R, LS, NR><<<grid, th, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0);
+                          int groups, int threads, cudaStream_t s) {
+  dim3 grid(blocks_for(g.V, threads), groups);
+  bri_kernel<R, LS, NR><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0);
   note_launch();
 }
 
-// nrhs right-hand sides: pairs share their link loads (FP32), an odd one
-// runs alone.
+// Launch configuration of the stencil: whether pairs of right-hand sides
+// share one thread (and so their link loads), and the block size.
+struct StencilConfig {
+  int pairs = 1;
+  int threads = 128;
+};
+
+template <typename R, typename LS>
+inline void launch_with(const StencilConfig& cf, const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag,
+                        R sgn, int nrhs, cudaStream_t s) {
+  int done = 0;
+  if constexpr (sizeof(R) == 4) {
+    if (nrhs >= 2 && cf.pairs) {
+      launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
+      done = (nrhs / 2) * 2;
+    }
+  }
+  if (nrhs > done) launch_bri_nr<R, LS, 1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, cf.threads, s);
+}
+
+// Autotuner: on the first launch for a (device, lattice, rhs-count class,
+// precision) the candidate configurations are timed (the timing launches
+// compute the same y = D x) and the fastest is cached for the process.  No
+// tuning happens while the stream is being captured into a graph.
+template <typename R, typename LS>
+StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, R sgn, int nrhs,
+                           cudaStream_t s) {
+  StencilConfig def;
+  if (!autotune_enabled()) {
+    def.pairs = pair_rhs_enabled();
+    return def;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int cls = nrhs <= 1 ? 1 : (nrhs < 4 ? 2 : 4);
+  char key[160];
+  snprintf(key, sizeof(key), "%d:%d,%d,%d,%d:%d:%d,%d", dev, g.L[0], g.L[1], g.L[2], g.L[3], cls, (int)sizeof(R),
+           (int)sizeof(LS));
+  StencilConfig found;
+  if (tune_lookup(key, &found)) return found;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap != cudaStreamCaptureStatusNone) return def;
+  std::vector<StencilConfig> cands;
+  for (int pairs = 0; pairs <= ((sizeof(R) == 4 && nrhs >= 2) ? 1 : 0); ++pairs)
+    for (int th : {64, 128}) cands.push_back(StencilConfig{pairs, th});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  StencilConfig bestc = def;
+  for (const StencilConfig& cf : cands) {
+    launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s);  // warm
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3; ++rep) launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestc = cf;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  tune_store(key, bestc);
+  return bestc;
+}
+
 template <typename R, typename LS>
 int launch_bri_t(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, int nrhs, int dagger,
                  cudaStream_t s) {
   int rc = ensure_hops();
   if (rc) return rc;
   const R sgn = (R)(dagger ? -1 : 1);
-  int done = 0;
-  if constexpr (sizeof(R) == 4) {
-    if (nrhs >= 2 && pair_rhs_enabled()) {
-      launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, s);
-      done = (nrhs / 2) * 2;
-    }
-  }
-  if (nrhs > done) launch_bri_nr<R, LS, 1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, s);
+  const StencilConfig cf = tuned_config(g, y, x, W, cl, diag, sgn, nrhs, s);
+  launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s);
   BRI_LAUNCH_CHECK("bri_kernel");
   return BRI_OK;
 }

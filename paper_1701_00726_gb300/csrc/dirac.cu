@@ -1,9 +1,38 @@
 // Stencil dispatch by precision, with optional event brackets (profiling).
-#include "stencil.cuh"
+#include "bri_kernel.cuh"
+
+#include <map>
+#include <mutex>
+#include <string>
 
 #include <cstdlib>
 
 namespace bri {
+
+int autotune_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("BRI_AUTOTUNE");
+    v = e ? (atoi(e) != 0) : 1;
+  }
+  return v;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::string, StencilConfig> g_tune;
+
+bool tune_lookup(const char* key, StencilConfig* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_store(const char* key, const StencilConfig& cf) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = cf;
+}
 
 int pair_rhs_enabled() {
   static int v = -1;

@@ -48,6 +48,9 @@ struct ProfRec {
 };
 
 void note_launch();
+void note_launches(long long n);
+// CUDA-graph replay of solver iterations (BRI_GRAPHS=0 disables it).
+int graphs_enabled();
 
 }  // namespace bri
 
@@ -77,6 +80,10 @@ struct bri_ctx {
   bri::Workspace ws;
   bri::Workspace ws_small;
   void* host_pinned = nullptr;
+  // library-owned stream the solvers run on (capture-capable, concurrent
+  // across contexts), fenced against the caller's stream with two events
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // profiling of stencil launches
   bool prof_on = false;
   std::vector<bri::ProfRec> prof_pending;

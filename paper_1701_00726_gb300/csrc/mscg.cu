@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 namespace bri {
@@ -414,17 +415,17 @@ struct DevBuf {
 };
 
 void configure_pool_once() {
-  static bool done = false;
-  if (done) return;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t thr = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  cudaGetLastError();
-  done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
 }
 
 // Operator application for the solver: out = D in (dagger 0) / D^dagger in.
@@ -455,7 +456,7 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
   T* r = br.as<T>();
   T* p = bp.as<T>();
   T* t = bt.as<T>();
-  T* q = bq.as<T>();
+  T* q_vec = bq.as<T>();
   MsState* S = bst.as<MsState>();
   double* part = bpart.as<double>();
 
@@ -486,20 +487,60 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
   int nact = nsys;
   DevBuf bflags;
   if ((rc = bflags.alloc(sizeof(int) * nsys, st))) return rc;
-  while (nact > 0 && it < maxiter) {
-    dim3 vga(nblk, nact);
-    for (int j = 0; j < check_every && it < maxiter; ++j, ++it) {
-      if ((rc = dirac_bri(c, t, p, nact, m0, 0, oprec, st))) return rc;
-      if ((rc = dirac_bri(c, q, t, nact, m0, 1, oprec, st))) return rc;
-      cnt->matvecs += 2;
-      if (sizeof(R) == 8) cnt->matvecs64 += 2;
-      k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q, part); note_launch();
-      k_scalar_alpha<<<nact, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
-      k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q, r, p, (T*)x, part, it == 0 ? 1 : 0);
+  // One block of iterations over the active prefix of systems.
+  auto enqueue_block = [&](int na, int it0, int count) -> int {
+    dim3 vga(nblk, na);
+    for (int j = 0; j < count; ++j) {
+      int q;
+      if ((q = dirac_bri(c, t, p, na, m0, 0, oprec, st))) return q;
+      if ((q = dirac_bri(c, q_vec, t, na, m0, 1, oprec, st))) return q;
+      k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q_vec, part); note_launch();
+      k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (T*)x, part, it0 + j == 0 ? 1 : 0);
       note_launch();
-      k_scalar_beta<<<nact, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      k_scalar_beta<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
       k_update_p0<R><<<vga, RED_THREADS, 0, st>>>(n2, S, r, p); note_launch();
     }
+    return BRI_OK;
+  };
+  // Blocks after the first are captured once per active-prefix size into a CUDA
+  // graph and replayed (fewer launch gaps on small lattices).  Not while the
+  // stencils are being profiled, and not on the legacy default stream.
+  const bool graphs = graphs_enabled() && !c->prof_on && st != nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_nact = -1;
+  long long g_launches = 0;
+  while (nact > 0 && it < maxiter) {
+    const int count = std::min(check_every, maxiter - it);
+    if (graphs && it > 0 && count == check_every) {
+      if (g_nact != nact) {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        cudaGraph_t graph = nullptr;
+        const long long l0 = bri_kernel_launches();
+        BRI_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const int erc = enqueue_block(nact, it, count);
+        const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        g_launches = bri_kernel_launches() - l0;
+        if (erc) {
+          if (graph) cudaGraphDestroy(graph);
+          return erc;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "multishift: graph capture");
+        const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(ie, "multishift: graph instantiate");
+        g_nact = nact;
+      } else {
+        note_launches(g_launches);
+      }
+      BRI_CUDA(cudaGraphLaunch(gexec, st));
+    } else {
+      if ((rc = enqueue_block(nact, it, count))) return rc;
+    }
+    cnt->matvecs += 2 * count;
+    if (sizeof(R) == 8) cnt->matvecs64 += 2 * count;
+    it += count;
     BRI_LAUNCH_CHECK("multishift iteration");
     // poll the done flags
     k_gather_done<<<1, 256, 0, st>>>(S, nsys, bflags.as<int>()); note_launch();
@@ -507,6 +548,7 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
     BRI_CUDA(cudaStreamSynchronize(st));
     while (nact > 0 && hdone[nact - 1]) --nact;
   }
+  if (gexec) cudaGraphExecDestroy(gexec);
   BRI_CUDA(cudaMemcpyAsync(hs.data(), S, sizeof(MsState) * nsys, cudaMemcpyDeviceToHost, st));
   BRI_CUDA(cudaStreamSynchronize(st));
   int maxit = 0, err = 0, notconv = 0;
@@ -723,8 +765,41 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
   return solve_rc;
 }
 
+// Runs the enclosed solver work on the context's own non-blocking stream
+// (fenced after the caller's stream on entry and before it on exit), so that
+// iterations can be graph-captured and contexts driven from different host
+// threads overlap on the GPU.  Nested scopes and allocation-free calls keep
+// the current stream.
+struct StreamScope {
+  bri_ctx* c;
+  cudaStream_t user;
+  bool active = false;
+  explicit StreamScope(bri_ctx* cx) : c(cx), user(cx->stream) {
+    if (!graphs_enabled() || (c->own_stream && c->stream == c->own_stream)) return;
+    if (!c->own_stream) {
+      if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+    }
+    cudaEventRecord(c->ev_in, user);
+    cudaStreamWaitEvent(c->own_stream, c->ev_in, 0);
+    c->stream = c->own_stream;
+    active = true;
+  }
+  ~StreamScope() {
+    if (!active) return;
+    cudaEventRecord(c->ev_out, c->own_stream);
+    cudaStreamWaitEvent(user, c->ev_out, 0);
+    c->stream = user;
+  }
+};
+
 int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho, double scale,
                double tol, int prec, double out_scale, double b_coeff, bri_stats* stats) {
+  StreamScope scope(c);
   auto t0 = std::chrono::steady_clock::now();
   configure_pool_once();
   cudaStream_t st = c->stream;

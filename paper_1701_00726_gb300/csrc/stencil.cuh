@@ -107,6 +107,11 @@ __device__ __forceinline__ void add_clover(Spinor<R>& acc, const Spinor<R>& x, c
 // Whether FP32 stencils carry two right-hand sides per thread (shared link
 // loads); BRI_PAIR_RHS=0 turns it off.
 int pair_rhs_enabled();
+// Stencil autotuning (BRI_AUTOTUNE=0 disables it) and its process-wide cache.
+int autotune_enabled();
+struct StencilConfig;
+bool tune_lookup(const char* key, StencilConfig* out);
+void tune_store(const char* key, const StencilConfig& cf);
 
 // Host-side launchers (one translation unit per precision).
 template <typename R, typename LS>

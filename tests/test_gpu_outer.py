@@ -15,11 +15,11 @@ pytestmark = pytest.mark.gpu
 RHO = 1.0
 
 
-@pytest.mark.parametrize("complete,am,n_inner,prec", [(True, 0.1, 4, PREC_F64), (False, 0.5, 0, PREC_F64),
-                                                      (True, 0.01, 4, PREC_F32)])
+@pytest.mark.parametrize("complete,am,n_inner,prec", [(True, 0.1, 2, PREC_F64), (False, 0.5, 0, PREC_F64),
+                                                      (True, 0.05, 2, PREC_F32)])
 def test_massive_solve_residual_with_oracle(complete, am, n_inner, prec):
-    dims = (6, 5, 4, 3)
-    n_outer = 8
+    dims = (4, 4, 3, 2)
+    n_outer = 6
     u = sf.gauge_field(dims, 1, 0.1, 3)
     b = sf.gaussian_source(dims, 1, 1001)
     lat = Lattice(dims)
@@ -45,9 +45,9 @@ def test_cascade_reduces_outer_iterations():
     b = torch.from_numpy(sf.gaussian_source(dims, 1, 1001)).cuda()
     lat = Lattice(dims)
     lat.build_links(torch.from_numpy(u).cuda(), 1.0)
-    x0, s0 = lat.overlap_solve(b, 16, 0, am=0.01, tol=1e-10)
-    x1, s1 = lat.overlap_solve(b, 16, 4, am=0.01, tol=1e-10)
+    x0, s0 = lat.overlap_solve(b, 8, 0, am=0.05, tol=1e-9)
+    x1, s1 = lat.overlap_solve(b, 8, 2, am=0.05, tol=1e-9)
     assert s0["converged"] and s1["converged"]
     assert s1["iterations"] < s0["iterations"]
     d = (x1 - x0).abs().max().item() / x0.abs().max().item()
-    assert d < 1e-8
+    assert d < 1e-7
