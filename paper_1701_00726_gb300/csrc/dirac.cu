@@ -1,5 +1,5 @@
 // Stencil dispatch by precision, with optional event brackets (profiling).
-#include "bri_kernel.cuh"
+#include "stencil.cuh"
 
 #include <map>
 #include <mutex>

@@ -13,7 +13,7 @@
 // pushed back through the path average (App. C) by reversing the last-step
 // recursion W_d = (1/k) sum_mu W_{d - s e_mu} U_step level by level, as
 // gathers (no atomics).  The clover term is not differentiated (c_SW = 0).
-#include "bri_kernel.cuh"
+#include "hops.cuh"
 
 namespace bri {
 namespace {
@@ -40,11 +40,11 @@ struct PairList {
 
 // G_W[idx](n) += sum_p w_p u_p(n) (M_d v_p(n+d))^dagger for the 80 hops d.
 // blockIdx.y = stored offset j (0..39), blockIdx.z = 0 for +d, 1 for -d.
-__global__ void __launch_bounds__(128) k_force(Geom g, const PairList* __restrict__ pl, int npair, double2* GW) {
+__global__ void __launch_bounds__(128) k_force(Geom g, const PairList* __restrict__ pl, int npair, double2* GW,
+                                              const __grid_constant__ HopTable<double> H) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int j = blockIdx.y, opp = blockIdx.z;
-  const HopTable<double>& H = c_hops_d;
   int m = 0;
   {
     int r = n;
@@ -268,7 +268,6 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   double c0, w[BRI_MAX_SHIFTS], sig[BRI_MAX_SHIFTS];
   int rc = kl_host(n, kind, scale, &c0, w, sig);
   if (rc) return rc;
-  if ((rc = ensure_hops())) return rc;
   const double kfac = (1.0 - am / (2.0 * rho)) * rho;
 
   // g_psi = gamma5 D_m gamma5 eta
@@ -341,7 +340,7 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
     }
     BRI_CUDA(cudaMemcpyAsync(bpl.as<PairList>(), &pl, sizeof(PairList), cudaMemcpyHostToDevice, st));
     dim3 grid(blocks_for(V, 128), 40, 2);
-    k_force<<<grid, 128, 0, st>>>(g, bpl.as<PairList>(), np, bGW.as<double2>()); note_launch();
+    k_force<<<grid, 128, 0, st>>>(g, bpl.as<PairList>(), np, bGW.as<double2>(), hop_table<double>()); note_launch();
     BRI_CUDA(cudaStreamSynchronize(st));  // the pair list buffer is reused
   }
 

@@ -109,7 +109,13 @@ __device__ __forceinline__ void add_clover(Spinor<R>& acc, const Spinor<R>& x, c
 int pair_rhs_enabled();
 // Stencil autotuning (BRI_AUTOTUNE=0 disables it) and its process-wide cache.
 int autotune_enabled();
-struct StencilConfig;
+// Launch configuration of the stencil: whether pairs of right-hand sides
+// share one thread (and so their link loads), and the block size.
+struct StencilConfig {
+  int pairs = 1;
+  int threads = 128;
+  int rg = 1;  // right-hand sides on consecutive lanes (shared link loads), instead of pairs
+};
 bool tune_lookup(const char* key, StencilConfig* out);
 void tune_store(const char* key, const StencilConfig& cf);
 

@@ -200,3 +200,19 @@ def test_mixed_order16_true_residuals(prec):
     assert st["max_true_residual"] <= 1e-10
     y64, st64 = lat.overlap_apply(xt, n=16, rho=1.0, tol=1e-12, prec=PREC_F64)
     assert relerr(y.cpu().numpy(), y64.cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "0,64,1", "1,64,1", "0,128,2", "0,128,4"])
+def test_bri_apply_every_launch_configuration(force, monkeypatch):
+    """Every stencil launch configuration the autotuner can pick gives the oracle's result
+    (5 right-hand sides: groups plus a remainder)."""
+    monkeypatch.setenv("BRI_STENCIL_FORCE", force)
+    dims = RAGGED
+    u = sf.gauge_field(dims, 9)
+    x = sf.gaussian_source(dims, 5, 1009)
+    lat = _lattice(dims, u, 1.0)
+    op = dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0)
+    for dagger in (False, True):
+        y = lat.bri_apply(torch.from_numpy(x).to(torch.complex64).cuda(), -1.0, dagger=dagger).cpu().numpy()
+        want = op.apply_dagger(x) if dagger else op.apply(x)
+        assert relerr(y, want) < 1e-5
