@@ -1,0 +1,233 @@
+// Brillouin stencil on the paired FP32 pipe (fma.rn.f32x2 through __ffma2_rn)
+// with the real and imaginary part of one complex number as the pair: a
+// spinor component loads as a native (re, im) register pair, and the complex
+// products become
+//   w x     = (w_re, w_re) (x_re, x_im) + (w_im, w_im) (-x_im, x_re),
+//   w^* x   = (w_re, w_re) (x_re, x_im) + (-w_im, -w_im) (-x_im, x_re),
+// so each paired FMA does two of the scalar kernel's FMAs in one issue slot.
+//
+// The arithmetic is that of the scalar kernel (Eq. def_bril, App. A): per
+// stored offset d the hop pair contributes a_k (P + Q) + c_k G (P - Q) with
+// P = W_d(n) x(n+d), Q = W_d(n-d)^dagger x(n-d).  Q is accumulated onto P
+// (u = P + Q) and the difference is formed as vn = u - 2P = -(P - Q); the
+// gamma part is applied to vn with negated weights.
+#pragma once
+
+#include "hops.cuh"
+
+namespace bri {
+
+// Per-offset weights as the constant pairs the paired arithmetic needs, for D
+// (dagger = 0) or D^dagger (dagger = 1), c_mu = sgn c_k s_mu:
+//   k[0] = (a, a),
+//   k[1] = (-c1, c1), k[2] = (c1, -c1),   gamma_1 rows on swapped (im, re) pairs
+//   k[3] = (c2, c2),  k[4] = (-c2, -c2),  gamma_2
+//   k[5] = (-c3, c3), k[6] = (c3, -c3),   gamma_3 rows on swapped pairs
+//   k[7] = (-c4, -c4)                     gamma_4
+// (signs for the vector vn = -(P - Q)).
+struct HopTableC2 {
+  int site_d[40][4];
+  float2 k[40][8];
+};
+
+inline HopTableC2 make_hop_table_c2(int dagger) {
+  const HopTable<float>& h = hop_table<float>();
+  HopTableC2 t;
+  const float sgn = dagger ? -1.f : 1.f;
+  for (int j = 0; j < 40; ++j) {
+    for (int mu = 0; mu < 4; ++mu) t.site_d[j][mu] = h.site_d[j][mu];
+    const float c1 = sgn * h.cs[j][0], c2 = sgn * h.cs[j][1], c3 = sgn * h.cs[j][2], c4 = sgn * h.cs[j][3];
+    t.k[j][0] = make_float2(h.a[j], h.a[j]);
+    t.k[j][1] = make_float2(-c1, c1);
+    t.k[j][2] = make_float2(c1, -c1);
+    t.k[j][3] = make_float2(c2, c2);
+    t.k[j][4] = make_float2(-c2, -c2);
+    t.k[j][5] = make_float2(-c3, c3);
+    t.k[j][6] = make_float2(c3, -c3);
+    t.k[j][7] = make_float2(-c4, -c4);
+  }
+  return t;
+}
+
+inline const HopTableC2& hop_table_c2(int dagger) {
+  static const HopTableC2 t0 = make_hop_table_c2(0);
+  static const HopTableC2 t1 = make_hop_table_c2(1);
+  return dagger ? t1 : t0;
+}
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 swp(float2 v) { return make_float2(v.y, v.x); }
+__device__ __forceinline__ float2 rot(float2 v) { return make_float2(-v.y, v.x); }  // i v
+
+// A spinor as (re, im) pairs, loaded with 16-byte loads.
+struct SpinorF2 {
+  float2 v[4][3];
+};
+__device__ __forceinline__ void load_spinor_f2(SpinorF2& s, const float* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float4 v = __ldg(q + i);
+    const int e0 = 2 * i, e1 = 2 * i + 1;
+    s.v[e0 / 3][e0 % 3] = make_float2(v.x, v.y);
+    s.v[e1 / 3][e1 % 3] = make_float2(v.z, v.w);
+  }
+}
+
+// acc += A u + (c G) v over one colour (four spins) with w = vn = -v and the
+// constant pairs of HopTableC2 (same spin pattern as gamma_term).
+__device__ __forceinline__ void pair_terms_c2(float2 acc[4], const float2 u[4], const float2 w[4], const float2* K) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) acc[s] = fma2(K[0], u[s], acc[s]);
+  const float2 s0 = swp(w[0]), s1 = swp(w[1]), s2 = swp(w[2]), s3 = swp(w[3]);
+  // gamma_1
+  acc[0] = fma2(K[1], s3, acc[0]);
+  acc[1] = fma2(K[1], s2, acc[1]);
+  acc[2] = fma2(K[2], s1, acc[2]);
+  acc[3] = fma2(K[2], s0, acc[3]);
+  // gamma_2
+  acc[0] = fma2(K[3], w[3], acc[0]);
+  acc[1] = fma2(K[4], w[2], acc[1]);
+  acc[2] = fma2(K[4], w[1], acc[2]);
+  acc[3] = fma2(K[3], w[0], acc[3]);
+  // gamma_3
+  acc[0] = fma2(K[5], s2, acc[0]);
+  acc[1] = fma2(K[6], s3, acc[1]);
+  acc[2] = fma2(K[6], s0, acc[2]);
+  acc[3] = fma2(K[5], s1, acc[3]);
+  // gamma_4
+  acc[0] = fma2(K[7], w[2], acc[0]);
+  acc[1] = fma2(K[7], w[3], acc[1]);
+  acc[2] = fma2(K[7], w[0], acc[2]);
+  acc[3] = fma2(K[7], w[1], acc[3]);
+}
+
+// One thread per site and right-hand side rhs0 + blockIdx.y.
+template <typename LS>
+__global__ void __launch_bounds__(128, 4)
+    bri_kernel_c2(Geom g, float* __restrict__ y, const float* __restrict__ x, const LS* __restrict__ W,
+                  const float* __restrict__ cl, float diag, int rhs0, const __grid_constant__ HopTableC2 H) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.V) return;
+  const int V = (int)g.V;
+  const int64_t rstride = g.V * 24;
+  const int64_t roff = (int64_t)(rhs0 + blockIdx.y) * rstride;
+  const float* xin = x + roff;
+  int co[4], L[4], str[4];
+  {
+    int r = n;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      co[mu] = r % g.L[mu];
+      r /= g.L[mu];
+    }
+    co[3] = r;
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    L[mu] = g.L[mu];
+    str[mu] = (int)g.str[mu];
+  }
+  float2 acc[4][3];
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) acc[s][aa] = make_float2(0.f, 0.f);
+  const float2 m2 = bc2(-2.f);
+#pragma unroll 1
+  for (int j = 0; j < 40; ++j) {
+    int mp = 0, mm = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int d = H.site_d[j][mu];
+      mp += wrap(co[mu] + d, L[mu]) * str[mu];
+      mm += wrap(co[mu] - d, L[mu]) * str[mu];
+    }
+    const LS* wj = W + (int64_t)j * 9 * V;
+    // P = W_d(n) x(n+d)
+    float2 P[4][3];
+    {
+      C<float> w[3][3];
+      load_link<float, LS>(w, wj + n, V);
+      SpinorF2 xs;
+      load_spinor_f2(xs, xin + (int64_t)mp * 24);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        float2 ix[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) ix[s] = rot(xs.v[s][b]);
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          const float2 wr = bc2(w[aa][b].re), wi = bc2(w[aa][b].im);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            P[s][aa] = b == 0 ? mul2(wr, xs.v[s][b]) : fma2(wr, xs.v[s][b], P[s][aa]);
+            P[s][aa] = fma2(wi, ix[s], P[s][aa]);
+          }
+        }
+      }
+    }
+    // u = P + W_d(n-d)^dagger x(n-d), vn = u - 2P
+    {
+      C<float> w[3][3];
+      load_link<float, LS>(w, wj + mm, V);
+      SpinorF2 xs;
+      load_spinor_f2(xs, xin + (int64_t)mm * 24);
+      float2 U[4][3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        float2 ix[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) ix[s] = rot(xs.v[s][b]);
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          const float2 wr = bc2(w[b][aa].re), nwi = bc2(-w[b][aa].im);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            U[s][aa] = fma2(wr, xs.v[s][b], b == 0 ? P[s][aa] : U[s][aa]);
+            U[s][aa] = fma2(nwi, ix[s], U[s][aa]);
+          }
+        }
+      }
+      float2 K[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) K[i] = H.k[j][i];
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        float2 u[4], vn[4], col[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          u[s] = U[s][aa];
+          vn[s] = fma2(m2, P[s][aa], U[s][aa]);
+          col[s] = acc[s][aa];
+        }
+        pair_terms_c2(col, u, vn, K);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc[s][aa] = col[s];
+      }
+    }
+  }
+  Spinor<float> xc, out;
+  load_spinor(xc, xin + (int64_t)n * 24);
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      out.v[s][aa].re = fmaf(diag, xc.v[s][aa].re, acc[s][aa].x);
+      out.v[s][aa].im = fmaf(diag, xc.v[s][aa].im, acc[s][aa].y);
+    }
+  if (cl) add_clover(out, xc, cl, g.V, n);
+  store_spinor(y + roff + (int64_t)n * 24, out);
+}
+
+template <typename LS>
+inline void launch_bri_c2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
+                          int dagger, int rhs0, int nrhs, int threads, cudaStream_t s) {
+  dim3 grid(blocks_for(g.V, threads), nrhs);
+  bri_kernel_c2<LS><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
+  note_launch();
+}
+
+}  // namespace bri

@@ -21,7 +21,7 @@
 // consecutive sites reads one contiguous segment per link element.
 #pragma once
 
-#include "hops.cuh"
+#include "bri_c2.cuh"
 
 #include <cstdio>
 #include <cstdlib>
@@ -87,25 +87,62 @@ __global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
       Spinor<R> xp, xm;
       load_spinor(xp, xin + r * rstride + (int64_t)mp * 24);
       load_spinor(xm, xin + r * rstride + (int64_t)mm * 24);
+      // u = P + Q (Q accumulated onto P), vn = u - 2P = -(P - Q): the gamma
+      // part takes vn with negated weights.
+      if constexpr (sizeof(R) == 8) {
+        // FP64 is bound by the FP64 pipe: gamma terms whose weight vanishes
+        // (s_mu = 0 for 4 - k of the four directions) are skipped with
+        // branches that are uniform across the grid.
+        C<R> vn[3][4];
 #pragma unroll
-      for (int aa = 0; aa < 3; ++aa) {
-        C<R> u[4], v[4], col[4];
+        for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          C<R> p = w[aa][0] * xp.v[s][0];
-          cfma(p, w[aa][1], xp.v[s][1]);
-          cfma(p, w[aa][2], xp.v[s][2]);
-          C<R> q{0, 0};
-          cfma_cj(q, wm[0][aa], xm.v[s][0]);
-          cfma_cj(q, wm[1][aa], xm.v[s][1]);
-          cfma_cj(q, wm[2][aa], xm.v[s][2]);
-          u[s] = p + q;
-          v[s] = p - q;
-          col[s] = acc[r].v[s][aa];
+          for (int s = 0; s < 4; ++s) {
+            C<R> p = w[aa][0] * xp.v[s][0];
+            cfma(p, w[aa][1], xp.v[s][1]);
+            cfma(p, w[aa][2], xp.v[s][2]);
+            C<R> q = p;
+            cfma_cj(q, wm[0][aa], xm.v[s][0]);
+            cfma_cj(q, wm[1][aa], xm.v[s][1]);
+            cfma_cj(q, wm[2][aa], xm.v[s][2]);
+            acc[r].v[s][aa].re = fma(a, q.re, acc[r].v[s][aa].re);
+            acc[r].v[s][aa].im = fma(a, q.im, acc[r].v[s][aa].im);
+            vn[aa][s] = C<R>{fma((R)-2, p.re, q.re), fma((R)-2, p.im, q.im)};
+          }
+        const R cn[4] = {-c1, -c2, -c3, -c4};
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          C<R> col[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) col[s] = acc[r].v[s][aa];
+          if (cn[0] != (R)0) gamma_term<1>(col, vn[aa], cn[0]);
+          if (cn[1] != (R)0) gamma_term<2>(col, vn[aa], cn[1]);
+          if (cn[2] != (R)0) gamma_term<3>(col, vn[aa], cn[2]);
+          if (cn[3] != (R)0) gamma_term<4>(col, vn[aa], cn[3]);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) acc[r].v[s][aa] = col[s];
         }
-        add_pair_terms(col, u, v, a, c1, c2, c3, c4);
+      } else {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) acc[r].v[s][aa] = col[s];
+        for (int aa = 0; aa < 3; ++aa) {
+          C<R> u[4], vn[4], col[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            C<R> p = w[aa][0] * xp.v[s][0];
+            cfma(p, w[aa][1], xp.v[s][1]);
+            cfma(p, w[aa][2], xp.v[s][2]);
+            C<R> q = p;
+            cfma_cj(q, wm[0][aa], xm.v[s][0]);
+            cfma_cj(q, wm[1][aa], xm.v[s][1]);
+            cfma_cj(q, wm[2][aa], xm.v[s][2]);
+            u[s] = q;
+            vn[s] = C<R>{fma((R)-2, p.re, q.re), fma((R)-2, p.im, q.im)};
+            col[s] = acc[r].v[s][aa];
+          }
+          add_pair_terms(col, u, vn, a, -c1, -c2, -c3, -c4);
+#pragma unroll
+          for (int s = 0; s < 4; ++s) acc[r].v[s][aa] = col[s];
+        }
       }
     }
   }
@@ -144,6 +181,9 @@ inline void launch_with(const StencilConfig& cf, const Geom& g, R* y, const R* x
     } else if (cf.rg == 2 && nrhs >= 2) {
       launch_bri_nr<R, LS, 1, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
       done = (nrhs / 2) * 2;
+    } else if (cf.pairs == 2) {
+      launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs, cf.threads, s);
+      done = nrhs;
     } else if (nrhs >= 2 && cf.pairs) {
       launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
       done = (nrhs / 2) * 2;
@@ -162,7 +202,8 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
   StencilConfig def;
   if (const char* f = getenv("BRI_STENCIL_FORCE")) {  // "pairs,threads,rg", read on every launch
     StencilConfig cf;
-    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && (cf.threads == 64 || cf.threads == 128) &&
+    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && cf.pairs >= 0 && cf.pairs <= 2 &&
+        (cf.threads == 64 || cf.threads == 128) &&
         (cf.rg == 1 || cf.rg == 2 || cf.rg == 4))
       return cf;
   }
@@ -184,6 +225,8 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
   std::vector<StencilConfig> cands;
   for (int pairs = 0; pairs <= ((sizeof(R) == 4 && nrhs >= 2) ? 1 : 0); ++pairs)
     for (int th : {64, 128}) cands.push_back(StencilConfig{pairs, th, 1});
+  if (sizeof(R) == 4)
+    for (int th : {64, 128}) cands.push_back(StencilConfig{2, th, 1});
   if (sizeof(R) == 4 && nrhs >= 2) cands.push_back(StencilConfig{0, 128, 2});
   if (sizeof(R) == 4 && nrhs >= 4) cands.push_back(StencilConfig{0, 128, 4});
   cudaEvent_t e0, e1;

@@ -67,31 +67,46 @@ __device__ __forceinline__ void spin_combine(Spinor<R>& chi, const Spinor<R>& x,
   }
 }
 
-// One colour of the accumulator (four spins): acc += a u + sum_mu cs_mu gamma_mu v
-// in the chiral basis (the same spin structure as spin_combine).
+// acc += c gamma_mu v over one colour (four spins), chiral basis (the same
+// spin structure as spin_combine): MU = 1..4.
+template <int MU, typename R>
+__device__ __forceinline__ void gamma_term(C<R> acc[4], const C<R> v[4], R c) {
+  if constexpr (MU == 1) {
+    acc[0].re = fma(c, v[3].im, acc[0].re); acc[0].im = fma(-c, v[3].re, acc[0].im);
+    acc[1].re = fma(c, v[2].im, acc[1].re); acc[1].im = fma(-c, v[2].re, acc[1].im);
+    acc[2].re = fma(-c, v[1].im, acc[2].re); acc[2].im = fma(c, v[1].re, acc[2].im);
+    acc[3].re = fma(-c, v[0].im, acc[3].re); acc[3].im = fma(c, v[0].re, acc[3].im);
+  } else if constexpr (MU == 2) {
+    acc[0].re = fma(-c, v[3].re, acc[0].re); acc[0].im = fma(-c, v[3].im, acc[0].im);
+    acc[1].re = fma(c, v[2].re, acc[1].re); acc[1].im = fma(c, v[2].im, acc[1].im);
+    acc[2].re = fma(c, v[1].re, acc[2].re); acc[2].im = fma(c, v[1].im, acc[2].im);
+    acc[3].re = fma(-c, v[0].re, acc[3].re); acc[3].im = fma(-c, v[0].im, acc[3].im);
+  } else if constexpr (MU == 3) {
+    acc[0].re = fma(c, v[2].im, acc[0].re); acc[0].im = fma(-c, v[2].re, acc[0].im);
+    acc[1].re = fma(-c, v[3].im, acc[1].re); acc[1].im = fma(c, v[3].re, acc[1].im);
+    acc[2].re = fma(-c, v[0].im, acc[2].re); acc[2].im = fma(c, v[0].re, acc[2].im);
+    acc[3].re = fma(c, v[1].im, acc[3].re); acc[3].im = fma(-c, v[1].re, acc[3].im);
+  } else {
+    acc[0].re = fma(c, v[2].re, acc[0].re); acc[0].im = fma(c, v[2].im, acc[0].im);
+    acc[1].re = fma(c, v[3].re, acc[1].re); acc[1].im = fma(c, v[3].im, acc[1].im);
+    acc[2].re = fma(c, v[0].re, acc[2].re); acc[2].im = fma(c, v[0].im, acc[2].im);
+    acc[3].re = fma(c, v[1].re, acc[3].re); acc[3].im = fma(c, v[1].im, acc[3].im);
+  }
+}
+
+// One colour of the accumulator (four spins): acc += a u + sum_mu cs_mu gamma_mu v.
 template <typename R>
 __device__ __forceinline__ void add_pair_terms(C<R> acc[4], const C<R> u[4], const C<R> v[4], R a, R c1, R c2,
                                                R c3, R c4) {
-  R r0 = fma(a, u[0].re, acc[0].re), i0 = fma(a, u[0].im, acc[0].im);
-  R r1 = fma(a, u[1].re, acc[1].re), i1 = fma(a, u[1].im, acc[1].im);
-  R r2 = fma(a, u[2].re, acc[2].re), i2 = fma(a, u[2].im, acc[2].im);
-  R r3 = fma(a, u[3].re, acc[3].re), i3 = fma(a, u[3].im, acc[3].im);
-  // gamma_1
-  r0 = fma(c1, v[3].im, r0); i0 = fma(-c1, v[3].re, i0); r1 = fma(c1, v[2].im, r1); i1 = fma(-c1, v[2].re, i1);
-  r2 = fma(-c1, v[1].im, r2); i2 = fma(c1, v[1].re, i2); r3 = fma(-c1, v[0].im, r3); i3 = fma(c1, v[0].re, i3);
-  // gamma_2
-  r0 = fma(-c2, v[3].re, r0); i0 = fma(-c2, v[3].im, i0); r1 = fma(c2, v[2].re, r1); i1 = fma(c2, v[2].im, i1);
-  r2 = fma(c2, v[1].re, r2); i2 = fma(c2, v[1].im, i2); r3 = fma(-c2, v[0].re, r3); i3 = fma(-c2, v[0].im, i3);
-  // gamma_3
-  r0 = fma(c3, v[2].im, r0); i0 = fma(-c3, v[2].re, i0); r1 = fma(-c3, v[3].im, r1); i1 = fma(c3, v[3].re, i1);
-  r2 = fma(-c3, v[0].im, r2); i2 = fma(c3, v[0].re, i2); r3 = fma(c3, v[1].im, r3); i3 = fma(-c3, v[1].re, i3);
-  // gamma_4
-  r0 = fma(c4, v[2].re, r0); i0 = fma(c4, v[2].im, i0); r1 = fma(c4, v[3].re, r1); i1 = fma(c4, v[3].im, i1);
-  r2 = fma(c4, v[0].re, r2); i2 = fma(c4, v[0].im, i2); r3 = fma(c4, v[1].re, r3); i3 = fma(c4, v[1].im, i3);
-  acc[0] = C<R>{r0, i0};
-  acc[1] = C<R>{r1, i1};
-  acc[2] = C<R>{r2, i2};
-  acc[3] = C<R>{r3, i3};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    acc[s].re = fma(a, u[s].re, acc[s].re);
+    acc[s].im = fma(a, u[s].im, acc[s].im);
+  }
+  gamma_term<1>(acc, v, c1);
+  gamma_term<2>(acc, v, c2);
+  gamma_term<3>(acc, v, c3);
+  gamma_term<4>(acc, v, c4);
 }
 
 }  // namespace bri

@@ -109,8 +109,9 @@ __device__ __forceinline__ void add_clover(Spinor<R>& acc, const Spinor<R>& x, c
 int pair_rhs_enabled();
 // Stencil autotuning (BRI_AUTOTUNE=0 disables it) and its process-wide cache.
 int autotune_enabled();
-// Launch configuration of the stencil: whether pairs of right-hand sides
-// share one thread (and so their link loads), and the block size.
+// Launch configuration of the FP32 stencil: pairs = 0 one right-hand side per
+// thread, 1 two per thread (shared link loads), 2 the paired-FP32 kernel
+// (bri_c2.cuh, one per thread); and the block size.
 struct StencilConfig {
   int pairs = 1;
   int threads = 128;

@@ -202,7 +202,7 @@ def test_mixed_order16_true_residuals(prec):
     assert relerr(y.cpu().numpy(), y64.cpu().numpy()) < 1e-9
 
 
-@pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "0,64,1", "1,64,1", "0,128,2", "0,128,4"])
+@pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "0,64,1", "1,64,1", "2,128,1", "2,64,1", "0,128,2", "0,128,4"])
 def test_bri_apply_every_launch_configuration(force, monkeypatch):
     """Every stencil launch configuration the autotuner can pick gives the oracle's result
     (5 right-hand sides: groups plus a remainder)."""
