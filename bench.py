@@ -139,10 +139,24 @@ def stencil_traffic():
         return None
 
 
+def stencil_traffic_per_launch(traffic, vol, nlaunch, units, prec):
+    """DRAM bytes per launch of the step's FP32 stencil launches from the committed
+    ncu capture: per-site link and clover bytes plus per-site-and-rhs spinor bytes
+    (both measured on a smaller lattice, scaled by the sites and rhs processed)."""
+    if traffic is None or prec != 1 or nlaunch <= 0:  # FP32 links (PREC_F32) only
+        return None
+    try:
+        per_site = float(traffic["links_clover_bytes_per_site"])
+        per_site_rhs = float(traffic["spinor_bytes_per_site_rhs"])
+    except (KeyError, TypeError, ValueError):
+        return None
+    return int(vol * per_site + units / nlaunch * per_site_rhs)
+
+
 def stencil_source_hash():
     """Hash of the FP32 stencil's sources (kernel header and shared helpers)."""
     h = hashlib.sha256()
-    for f in ("bri_kernel.cuh", "stencil.cuh", "cplx.cuh"):
+    for f in ("bri_kernel.cuh", "bri_c2.cuh", "hops.cuh", "stencil.cuh", "cplx.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1701_00726_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -348,13 +362,14 @@ def main():
     t_hbm = alg_bytes / (peak * 1e9)
     t_alu = alg_flops / (fp32_peak * 1e12)
     traffic = stencil_traffic()
-    common = {"kernel": "bri_kernel<float," + ("bf16x2" if prec == PREC_F32_BF16 else "float2") + ",1|2>",
+    lt = "bf16x2" if prec == PREC_F32_BF16 else "float2"
+    common = {"kernel": f"bri_kernel<float,{lt},1|2> | bri_kernel_c2<{lt}> (autotuned per rhs count)",
               "launches": nlaunch, "avg_launch_ms": round(kms / max(nlaunch, 1), 4),
               "avg_rhs_per_launch": round(units / max(nlaunch, 1) / vol, 3),
               "alg_bytes_per_launch": int(alg_bytes / max(nlaunch, 1)),
               "alg_flops_per_launch": int(alg_flops / max(nlaunch, 1)),
               "stencil_share_of_step": round(ksec / elapsed, 4) if world == 1 else None,
-              "traffic": None if traffic is None or nrhs != 1 else traffic.get("dram_bytes_per_launch")}
+              "traffic": stencil_traffic_per_launch(traffic, vol, nlaunch, units, prec)}
     if t_alu >= t_hbm:
         achieved = alg_flops / ksec / 1e12 if ksec > 0 else 0.0
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
