@@ -12,13 +12,15 @@
 // n-d, daggered (W_{82-nu}(n) = W_nu(n-d)^dagger).  Both hops of a pair have
 // the same weights a_k, c_k and spin matrix G = sum_mu s_mu gamma_mu up to the
 // sign of G, so the two source spinors are colour-transported first
-// (P = W x(n+d), Q = W'^dagger x(n-d)) and the spin structure is applied once to
-// their sum and difference: acc += a_k (P + Q) + c_k G (P - Q) (in the chiral
-// basis gamma_mu only permutes spin components with phases +-1, +-i).  The per-offset constants come from a
-// small table passed as a __grid_constant__ kernel parameter; the loop is not unrolled so that the
-// compiler does not hoist loads across hops, which keeps the live register set
-// (and so the occupancy) bounded.  Links are structure-of-arrays, so a warp of
-// consecutive sites reads one contiguous segment per link element.
+// (P = W x(n+d), Q = W'^dagger x(n-d), Q accumulated onto P) and the spin
+// structure is applied once: acc += a_k (P + Q) + c_k G (P - Q), with
+// P - Q = 2P - (P + Q) (in the chiral basis gamma_mu only permutes spin
+// components with phases +-1, +-i).  The FP64 instance skips the gamma terms
+// whose s_mu vanishes.  The per-offset constants come from a small table
+// passed as a __grid_constant__ kernel parameter; the loop is not unrolled so
+// that the compiler does not hoist loads across hops, which keeps the live
+// register set (and so the occupancy) bounded.  Links are structure-of-arrays,
+// so a warp of consecutive sites reads one contiguous segment per link element.
 #pragma once
 
 #include "bri_c2.cuh"
