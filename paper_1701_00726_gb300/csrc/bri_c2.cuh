@@ -145,12 +145,11 @@ __global__ void __launch_bounds__(128, 4)
       mp += wrap(co[mu] + d, L[mu]) * str[mu];
       mm += wrap(co[mu] - d, L[mu]) * str[mu];
     }
-    const LS* wj = W + (int64_t)j * 9 * V;
     // P = W_d(n) x(n+d)
     float2 P[4][3];
     {
       C<float> w[3][3];
-      load_link<float, LS>(w, wj + n, V);
+      load_stored_link<float, LS>(w, W, j, n, V);
       SpinorF2 xs;
       load_spinor_f2(xs, xin + (int64_t)mp * 24);
 #pragma unroll
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(128, 4)
     // u = P + W_d(n-d)^dagger x(n-d), vn = u - 2P
     {
       C<float> w[3][3];
-      load_link<float, LS>(w, wj + mm, V);
+      load_stored_link<float, LS>(w, W, j, mm, V);
       SpinorF2 xs;
       load_spinor_f2(xs, xin + (int64_t)mm * 24);
       float2 U[4][3];

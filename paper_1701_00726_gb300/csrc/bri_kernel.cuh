@@ -75,15 +75,14 @@ __global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
     }
     const R a = H.a[j];
     const R c1 = sgn * H.cs[j][0], c2 = sgn * H.cs[j][1], c3 = sgn * H.cs[j][2], c4 = sgn * H.cs[j][3];
-    const LS* wj = W + (int64_t)j * 9 * V;
     // The pair of opposite hops shares a, c and G = sum_mu s_mu gamma_mu:
     //   W x+ M_d + W'^dagger M_{-d} x- = a (P + Q) + c G (P - Q),
     //   P = W_d(n) x(n+d),  Q = W_d(n-d)^dagger x(n-d)   (M_{+-d} = a +- c G).
     // Both links and both source spinors are loaded before any arithmetic, so
     // one memory latency is exposed per pair of hops.
     C<R> w[3][3], wm[3][3];
-    load_link<R, LS>(w, wj + n, V);
-    load_link<R, LS>(wm, wj + mm, V);
+    load_stored_link<R, LS>(w, W, j, n, V);
+    load_stored_link<R, LS>(wm, W, j, mm, V);
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       Spinor<R> xp, xm;

@@ -63,9 +63,10 @@ struct bri_ctx {
   bool have_links = false;
   bool have_clover = false;
   double c_sw = 0.0;
-  // Stored off-axis links, structure-of-arrays [40][9][V] complex (FP64 /
-  // FP32 / BF16): element (nu, e, n) sits at (nu*9 + e)*V + n so that a warp
-  // of consecutive sites reads one contiguous 256/512/128-byte segment.
+  // Stored off-axis links, structure-of-arrays: FP64 and BF16 [40][9][V]
+  // complex, element (nu, e, n) at (nu*9 + e)*V + n; FP32 [40][5][V] pairs of
+  // complex (elements 2k, 2k+1 in one 16-byte word, tenth slot padding).  A
+  // warp of consecutive sites reads one contiguous segment per load.
   double2* W64 = nullptr;
   float2* W32 = nullptr;
   __nv_bfloat162* W16 = nullptr;

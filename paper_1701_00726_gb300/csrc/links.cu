@@ -148,12 +148,15 @@ __global__ void levelk_kernel(Geom g, const double2* __restrict__ U64, double2* 
   store_soa(T + (int64_t)nu * 9 * g.V, g.V, n, acc);
 }
 
+// FP32 copy in the paired layout [40][5][V] float4 (elements 2k, 2k+1 of one
+// site in one 16-byte word); BF16 copy in the FP64 layout [40][9][V].
 __global__ void narrow_links_kernel(int64_t count, const double2* __restrict__ W64, float2* W32,
-                                    __nv_bfloat162* W16) {
+                                    __nv_bfloat162* W16, int64_t V) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= count) return;
   double2 v = W64[i];
-  W32[i] = make_float2((float)v.x, (float)v.y);
+  const int64_t nu9e = i / V, n = i - nu9e * V, nu = nu9e / 9, e = nu9e - nu * 9;
+  W32[((nu * 5 + e / 2) * V + n) * 2 + (e & 1)] = make_float2((float)v.x, (float)v.y);
   W16[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
 }
 
@@ -286,7 +289,7 @@ int launch_build_links(bri_ctx* c, const double* U, double c_sw) {
   };
   int rc;
   if ((rc = alloc((void**)&c->W64, sizeof(double2) * 360 * V))) return rc;
-  if ((rc = alloc((void**)&c->W32, sizeof(float2) * 360 * V))) return rc;
+  if ((rc = alloc((void**)&c->W32, sizeof(float2) * 400 * V))) return rc;
   if ((rc = alloc((void**)&c->W16, sizeof(__nv_bfloat162) * 360 * V))) return rc;
   if ((rc = alloc((void**)&c->U64, sizeof(double2) * 36 * V))) return rc;
   if ((rc = alloc((void**)&c->U32, sizeof(float2) * 36 * V))) return rc;
@@ -298,7 +301,7 @@ int launch_build_links(bri_ctx* c, const double* U, double c_sw) {
                                                        (c->flags & BRI_ANTIPERIODIC_T) ? 1 : 0); note_launch();
   if ((rc = build_transporters(c, T))) return rc;
   BRI_CUDA(cudaMemcpyAsync(c->W64, T, sizeof(double2) * 360 * V, cudaMemcpyDeviceToDevice, st));
-  narrow_links_kernel<<<blocks_for(360 * V, 256), 256, 0, st>>>(360 * V, c->W64, c->W32, c->W16); note_launch();
+  narrow_links_kernel<<<blocks_for(360 * V, 256), 256, 0, st>>>(360 * V, c->W64, c->W32, c->W16, V); note_launch();
   BRI_LAUNCH_CHECK("narrow_links_kernel");
   c->have_clover = false;
   c->c_sw = c_sw;

@@ -66,6 +66,26 @@ __device__ __forceinline__ void load_link(C<R> w[3][3], const LS* __restrict__ p
   }
 }
 
+// Stored link of offset j at site m.  FP64 and BF16 links are [40][9][V]
+// (element e at (j*9 + e)*V + m); FP32 links pair consecutive elements in one
+// 16-byte word, [40][5][V] float4 (elements 2k, 2k+1; the tenth slot is
+// padding), so a link takes five 16-byte loads instead of nine 8-byte ones.
+template <typename R, typename LS>
+__device__ __forceinline__ void load_stored_link(C<R> w[3][3], const LS* __restrict__ W, int j, int m, int V) {
+  if constexpr (sizeof(R) == 4 && sizeof(LS) == 8) {
+    const float4* q = reinterpret_cast<const float4*>(W) + (int64_t)j * 5 * V + m;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float4 v = __ldg(q + (int64_t)k * V);
+      const int e0 = 2 * k, e1 = 2 * k + 1;
+      w[e0 / 3][e0 % 3] = C<R>{v.x, v.y};
+      if (e1 < 9) w[e1 / 3][e1 % 3] = C<R>{v.z, v.w};
+    }
+  } else {
+    load_link<R, LS>(w, W + (int64_t)j * 9 * V + m, V);
+  }
+}
+
 __device__ __forceinline__ int wrap(int c, int L) { return c < 0 ? c + L : (c >= L ? c - L : c); }
 
 // Packed Hermitian 6x6 times a 6-vector: diag reals [0..5], then upper complex.
