@@ -8,7 +8,8 @@
  *           - (c_SW/2) sum_{mu<nu} sigma_{mu nu} F_{mu nu}          (Eq. def_bril)
  *   D_wil = sum_mu gamma_mu nabla^std_mu - (1/2) Delta^std + m0 - clover
  *                                                                   (Eq. def_wils)
- *   D_ov  = rho [1 + gamma5 f_nn(H)],  H = gamma5 D_bri(m0 = -rho)  (Eq. def_over)
+ *   D_ov  = rho [1 + gamma5 f_nn(H)],  H = gamma5 D_K(m0 = -rho)    (Eq. def_over)
+ *           with the kernel D_K = D_bri (default) or D_wil (bri_set_kernel)
  *   f_nn(x) = x [c0 + sum_i w_i / (x^2 + sigma_i)]                  (Eq. KLnn_parfrac)
  *
  * with a = 1.  Conventions shared by every call:
@@ -58,6 +59,10 @@ extern "C" {
 /* bri_create flags */
 #define BRI_ANTIPERIODIC_T 1 /* antiperiodic time direction (sign of U_t on the last slice) */
 
+/* Kernel operator of the overlap solvers (bri_set_kernel) */
+#define BRI_KERNEL_BRILLOUIN 0 /* D_bri, Eq. def_bril (the default) */
+#define BRI_KERNEL_WILSON 1    /* D_wil, Eq. def_wils */
+
 /* Kenney-Laub family for kl_coeffs / solvers */
 #define BRI_KL_DIAGONAL 0 /* f_nn = g_{2n+1}: constant term + n shifts (Tab. 5) */
 #define BRI_KL_UPPER 1    /* f_{n-1,n} = g_{2n}: n shifts, no constant (Tab. 6) */
@@ -89,6 +94,14 @@ int bri_create(bri_ctx** ctx, const int dims[4], int flags, void* stream);
 void bri_destroy(bri_ctx* ctx);
 int bri_set_stream(bri_ctx* ctx, void* stream);
 
+/* Select the kernel operator D_K of the overlap solvers of this context
+ * (sign_apply_multishift, overlap_apply, overlap_apply_batch, overlap_solve,
+ * overlap_grad, sign_apply_multishift_noalloc): BRI_KERNEL_BRILLOUIN (default)
+ * or BRI_KERNEL_WILSON.  The paper compares both kernels inside the overlap
+ * (Eqs. def_wils, def_bril inside Eq. def_over; Secs. 5-8).  Both use the same
+ * clover coefficient and, for the Wilson kernel, the thin links. */
+int bri_set_kernel(bri_ctx* ctx, int kernel);
+
 /* Build the 40 stored path-averaged off-axis links W_nu(n), nu = 1..40
  * (App. C: the average over the k! shortest paths of the link products, no
  * SU(3) back-projection) in FP64, FP32 and BF16 storage, the thin-link copy
@@ -118,7 +131,7 @@ int wils_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, double m0, int da
  * i = 0..n-1, shifts increasing.  Writes n entries into w and sigma. */
 int kl_coeffs(int n, int kind, double scale, double* c0, double* w, double* sigma);
 
-/* y = gamma5 f(H) x = D r(D^dagger D) x, H = gamma5 D_bri(m0 = -rho), with
+/* y = gamma5 f(H) x = D r(D^dagger D) x, H = gamma5 D_K(m0 = -rho), with
  * r(s) = c0 + sum_i w_i/(s+sigma_i) evaluated by one multi-shift CG
  * (Sec. 3.3, Sec. 4.1) to relative residual tol on every shift.
  * x, y: device complex128 [nrhs][V][4][3].  prec: BRI_PREC_F64 (all FP64) or
@@ -187,11 +200,14 @@ int overlap_grad(bri_ctx* ctx, void* g_psi, void* g_U, const void* eta, const vo
  *
  * All solver workspace comes from one 32 MiB static device array that every
  * device loading the library holds until exit.  Limit: V * nrhs * (2n + 3) *
- * 192 bytes plus ~64 KB of state must fit in it (e.g. 8^4 with nrhs = 1 and
- * n <= 20, or 4^4 with nrhs <= 16 at n = 16); larger problems are rejected
- * with BRI_ERR_INVALID and a message.  The first call on a device looks the
- * array's address up (cudaGetSymbolAddress) and should come before any stream
- * capture.  Every call reuses the same array and leaves its contents behind;
+ * 192 bytes plus 64 KB + 4 KB * nrhs of state must fit in it (e.g. 8^4 with
+ * nrhs = 1 and n <= 19, or 4^4 with nrhs <= 16 at n = 16); larger problems
+ * are rejected with BRI_ERR_INVALID and a message.  The array's device address
+ * is looked up (cudaGetSymbolAddress) by bri_build_links on the device that is
+ * current then, which under lazy module loading is also when its 32 MiB are
+ * committed; a call on a device where no links were built does that set-up
+ * itself and should then come before any stream capture.  Every call reuses
+ * the same array and leaves its contents behind;
  * the solver initialises everything it reads, but two calls whose work
  * overlaps on one device (other streams or host threads) race on it.
  * x, y: device complex128 [nrhs][V][4][3]; st may be NULL (true residuals are
@@ -210,6 +226,11 @@ int bri_profile_read(bri_ctx* ctx, int op, int prec, long long* launches, double
 
 /* Process-wide number of CUDA kernels this library has launched so far. */
 long long bri_kernel_launches(void);
+
+/* Process-wide number of device allocations this library has made so far
+ * (link and clover storage, solver workspaces).  Diagnostic: the
+ * allocation-free entry point leaves it unchanged. */
+long long bri_device_allocations(void);
 
 /* Thread-local description of the last error (never NULL). */
 const char* bri_last_error(void);

@@ -15,11 +15,12 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KL_DIAGONAL, KL_UPPER, PREC_F32, PREC_F32_BF16, PREC_F64,
-                   BriError, BriStats, kl_coeffs)
+from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KERNEL_BRILLOUIN, KERNEL_WILSON, KL_DIAGONAL, KL_UPPER,
+                   PREC_F32, PREC_F32_BF16, PREC_F64, BriError, BriStats, kl_coeffs)
 
-__all__ = ["Lattice", "overlap", "OverlapFunction", "overlap_apply_batch", "kl_coeffs", "BriError", "BriStats", "PREC_F64", "PREC_F32", "PREC_F32_BF16",
-           "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T"]
+__all__ = ["Lattice", "overlap", "OverlapFunction", "overlap_apply_batch", "kl_coeffs", "BriError", "BriStats",
+           "PREC_F64", "PREC_F32", "PREC_F32_BF16", "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T", "KERNEL_BRILLOUIN",
+           "KERNEL_WILSON"]
 
 
 def _torch():
@@ -78,6 +79,11 @@ class Lattice:
             raise BriError("gauge field must have V*4*3*3 elements")
         _lib.check(self.lib.bri_build_links(self._h, ctypes.c_void_p(u.data_ptr()), float(c_sw)), "bri_build_links")
 
+    def set_kernel(self, kernel):
+        """Kernel operator of the overlap solvers: KERNEL_BRILLOUIN ("bri") or KERNEL_WILSON ("wil")."""
+        k = {"bri": KERNEL_BRILLOUIN, "wil": KERNEL_WILSON}.get(kernel, kernel)
+        _lib.check(self.lib.bri_set_kernel(self._h, int(k)), "bri_set_kernel")
+
     def links(self):
         """Stored off-axis links, complex128 [V, 40, 3, 3] (App. C layout)."""
         torch = _torch()
@@ -100,6 +106,10 @@ class Lattice:
     @staticmethod
     def kernel_launches():
         return int(_lib.load().bri_kernel_launches())
+
+    @staticmethod
+    def device_allocations():
+        return int(_lib.load().bri_device_allocations())
 
     @staticmethod
     def _prec_for(x, bf16_links):

@@ -20,6 +20,8 @@ PREC_F64 = 0
 PREC_F32 = 1
 PREC_F32_BF16 = 2
 ANTIPERIODIC_T = 1
+KERNEL_BRILLOUIN = 0
+KERNEL_WILSON = 1
 KL_DIAGONAL = 0
 KL_UPPER = 1
 MAX_SHIFTS = 32
@@ -61,6 +63,7 @@ _SIGS = {
                                   ctypes.c_void_p]),
     "bri_destroy": (None, [ctypes.c_void_p]),
     "bri_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "bri_set_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bri_build_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "bri_get_links": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "bri_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
@@ -94,6 +97,7 @@ _SIGS = {
     "bri_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "bri_kernel_launches": (ctypes.c_longlong, []),
+    "bri_device_allocations": (ctypes.c_longlong, []),
     "bri_last_error": (ctypes.c_char_p, []),
 }
 

@@ -15,8 +15,10 @@ namespace bri {
 
 static thread_local std::string g_err = "no error";
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_dev_allocs{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_device_alloc() { g_dev_allocs.fetch_add(1, std::memory_order_relaxed); }
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int graphs_enabled() {
@@ -202,6 +204,15 @@ int bri_set_stream(bri_ctx* c, void* stream) {
   return BRI_OK;
 }
 
+int bri_set_kernel(bri_ctx* c, int kernel) {
+  if (!c || (kernel != BRI_KERNEL_BRILLOUIN && kernel != BRI_KERNEL_WILSON)) {
+    set_error("bri_set_kernel: null context or unknown kernel");
+    return BRI_ERR_INVALID;
+  }
+  c->kernel = kernel;
+  return BRI_OK;
+}
+
 int bri_build_links(bri_ctx* c, const double* U, double c_sw) {
   if (!c || !U) {
     set_error("bri_build_links: null argument");
@@ -211,7 +222,10 @@ int bri_build_links(bri_ctx* c, const double* U, double c_sw) {
     set_error("bri_build_links: c_sw must be finite");
     return BRI_ERR_INVALID;
   }
-  return launch_build_links(c, U, c_sw);
+  int rc = launch_build_links(c, U, c_sw);
+  if (rc) return rc;
+  // set-up of the allocation-free entry point on this device
+  return noalloc_prepare_current_device();
 }
 
 int bri_get_links(bri_ctx* c, double* W) {
@@ -321,6 +335,10 @@ int overlap_grad(bri_ctx* c, void* g_psi, void* g_U, const void* eta, const void
     set_error("overlap_grad: the clover term is not differentiated; build the links with c_sw = 0");
     return BRI_ERR_INVALID;
   }
+  if (c->kernel != BRI_KERNEL_BRILLOUIN) {
+    set_error("overlap_grad: only the Brillouin kernel is differentiated");
+    return BRI_ERR_INVALID;
+  }
   if (!std::isfinite(am) || am >= 2.0 * rho) {
     set_error("overlap_grad: the traditional massive form needs am < 2 rho");
     return BRI_ERR_INVALID;
@@ -381,6 +399,11 @@ int overlap_apply_batch(bri_ctx* const* ctxs, int nctx, void* const* ys, const v
   }
   int dev = 0;
   cudaGetDevice(&dev);
+  // autotune every lattice's stencil launches first, one lattice at a time
+  for (int i = 0; i < nctx; ++i) {
+    int rc = pretune_stencils(ctxs[i], prec);
+    if (rc) return rc;
+  }
   std::vector<int> rcs(nctx, BRI_OK);
   std::vector<std::string> errs(nctx);
   std::vector<std::thread> pool;
@@ -430,5 +453,7 @@ int bri_profile_read(bri_ctx* c, int op, int prec, long long* launches, double* 
 }
 
 long long bri_kernel_launches(void) { return g_launches.load(); }
+
+long long bri_device_allocations(void) { return g_dev_allocs.load(); }
 
 }  // extern "C"

@@ -27,6 +27,7 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 namespace bri {
@@ -223,6 +224,10 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   if (cap != cudaStreamCaptureStatusNone) return def;
+  // One timing loop at a time in the process (host threads driving other
+  // lattices would otherwise time their candidates against each other).
+  std::lock_guard<std::mutex> tune_lock(tune_mutex());
+  if (tune_lookup(key, &found)) return found;
   std::vector<StencilConfig> cands;
   for (int pairs = 0; pairs <= ((sizeof(R) == 4 && nrhs >= 2) ? 1 : 0); ++pairs)
     for (int th : {64, 128}) cands.push_back(StencilConfig{pairs, th, 1});

@@ -34,6 +34,48 @@ void tune_store(const char* key, const StencilConfig& cf) {
   g_tune[key] = cf;
 }
 
+int dirac_kernel(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec, cudaStream_t s) {
+  if (c->kernel == BRI_KERNEL_WILSON) return dirac_wil(c, y, x, nrhs, m0, dagger, prec, s);
+  return dirac_bri(c, y, x, nrhs, m0, dagger, prec, s);
+}
+
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+
+// Runs the stencil once for every right-hand-side class (1, 2-3, >= 4) and
+// precision a solve of precision prec uses, so that the autotuner's choices
+// for this lattice are made now, with nothing else on the GPU.
+int pretune_stencils(bri_ctx* c, int prec) {
+  if (!autotune_enabled() || !c->have_links) return BRI_OK;
+  cudaStream_t s = c->stream;
+  const int64_t nreal = c->g.V * 24;
+  void* buf = nullptr;
+  const size_t bytes = sizeof(double) * nreal * 4 * 2;
+  cudaError_t e = cudaMallocAsync(&buf, bytes, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pretune: cudaMallocAsync");
+  note_device_alloc();
+  int rc = BRI_OK;
+  if ((e = cudaMemsetAsync(buf, 0, bytes, s)) != cudaSuccess) rc = cuda_fail(e, "pretune: cudaMemsetAsync");
+  int precs[3] = {BRI_PREC_F64, -1, -1};
+  if (prec != BRI_PREC_F64) {
+    precs[1] = BRI_PREC_F32;
+    if (prec == BRI_PREC_F32_BF16) precs[2] = BRI_PREC_F32_BF16;
+  }
+  for (int pi = 0; pi < 3 && rc == BRI_OK; ++pi) {
+    if (precs[pi] < 0) continue;
+    const size_t half = precs[pi] == BRI_PREC_F64 ? sizeof(double) * nreal * 4 : sizeof(float) * nreal * 4;
+    for (int nr : {1, 2, 4}) {
+      rc = dirac_bri(c, (char*)buf + half, buf, nr, -1.0, 0, precs[pi], s);
+      if (rc) break;
+    }
+  }
+  cudaFreeAsync(buf, s);
+  cudaGetLastError();
+  return rc;
+}
+
 int pair_rhs_enabled() {
   static int v = -1;
   if (v < 0) {

@@ -6,7 +6,8 @@
 // dL = Re sum tr(G^dagger dU)).  With k = (1 - am/(2 rho)) rho,
 // x_i = (A + sigma_i)^{-1} psi, z_i = (A + sigma_i)^{-1} D^dagger eta and
 // y = c0 psi + sum_i w_i x_i (both multi-shift solves share the shifts):
-//   g_psi = D_m^dagger eta = gamma5 D_m gamma5 eta,
+//   g_psi = D_m^dagger eta = k (eta + r(A) D^dagger eta) + am eta
+//         = k (eta + c0 D^dagger eta + sum_i w_i z_i) + am eta   (z_i reused),
 //   dL = k Re<eta, dD y> - k sum_i w_i (Re<D x_i, dD z_i> + Re<D z_i, dD x_i>).
 // Each term Re<u, dD v> gives every transporter W_d(n) the gradient
 // G_W = u(n) (M_d v(n+d))^dagger (kernel k_force); the gradients are then
@@ -17,20 +18,6 @@
 
 namespace bri {
 namespace {
-
-// out = gamma5 in (spins 2 and 3 negated), FP64 spinors
-__global__ void k_gamma5(int64_t nsite_rhs, const double2* __restrict__ in, double2* out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nsite_rhs * 12;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int spin = (int)((i % 12) / 3);
-    double2 v = in[i];
-    if (spin >= 2) {
-      v.x = -v.x;
-      v.y = -v.y;
-    }
-    out[i] = v;
-  }
-}
 
 struct PairList {
   const double* u[512];
@@ -241,10 +228,17 @@ struct Buf {
       set_error(std::string("cudaMallocAsync failed: ") + cudaGetErrorString(e));
       return BRI_ERR_OOM;
     }
+    note_device_alloc();
     return BRI_OK;
   }
   template <typename T> T* as() const { return (T*)p; }
 };
+
+// y = a x + b y (real coefficients, FP64)
+__global__ void k_axpby_real(int64_t n, double a, const double* __restrict__ x, double b, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
 
 // acc = c0 b + sum_i w_i X_i for systems s < nout of an X with nsys systems per shift
 __global__ void k_rational_sub(int64_t nreal, int nsys, int nshift, double c0, const double* __restrict__ w,
@@ -270,18 +264,7 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   if (rc) return rc;
   const double kfac = (1.0 - am / (2.0 * rho)) * rho;
 
-  // g_psi = gamma5 D_m gamma5 eta
-  Buf bg5;
-  if ((rc = bg5.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-  k_gamma5<<<1024, 256, 0, st>>>(V * nrhs, (const double2*)eta, bg5.as<double2>()); note_launch();
-  bri_stats st_ov;
-  memset(&st_ov, 0, sizeof(st_ov));
-  if (stats) st_ov.maxiter = stats->maxiter;
-  rc = sign_apply(c, (double2*)g_psi, bg5.as<double2>(), nrhs, n, kind, rho, scale, tol, prec, kfac, kfac + am, &st_ov);
-  if (rc < 0) return rc;
-  int solve_rc = rc;
-  k_gamma5<<<1024, 256, 0, st>>>(V * nrhs, (const double2*)g_psi, (double2*)g_psi); note_launch();
-
+  int solve_rc = BRI_OK;
   // shifted solves for psi and D^dagger eta (2 nrhs systems, same shifts)
   const int nsys = 2 * nrhs;
   Buf bb, bX, bDX, by;
@@ -305,6 +288,13 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   BRI_CUDA(cudaMemcpyAsync(bw.as<double>(), w, sizeof(double) * n, cudaMemcpyHostToDevice, st));
   if ((rc = by.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
   k_rational_sub<<<dim3(256, nrhs), 256, 0, st>>>(nreal, nsys, n, c0, bw.as<double>(), psi, X, by.as<double>());
+  note_launch();
+  // g_psi = k eta + am eta + k (c0 D^dagger eta + sum_i w_i z_i): the rational of the
+  // second half of the systems (right-hand sides D^dagger eta), then the axpy
+  k_rational_sub<<<dim3(256, nrhs), 256, 0, st>>>(nreal, nsys, n, c0, bw.as<double>(), bb.as<double>() + nreal * nrhs,
+                                                  X + nreal * nrhs, g_psi);
+  note_launch();
+  k_axpby_real<<<1024, 256, 0, st>>>(nreal * nrhs, kfac + am, eta, kfac, g_psi);
   note_launch();
   if ((rc = bDX.alloc(sizeof(double) * nreal * nsys * n, st))) return rc;
   if ((rc = dirac_bri(c, bDX.as<double>(), X, nsys * n, m0, 0, BRI_PREC_F64, st))) return rc;
@@ -363,10 +353,10 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   BRI_LAUNCH_CHECK("overlap_grad backward");
   BRI_CUDA(cudaStreamSynchronize(st));
   if (stats) {
-    stats->iterations = std::max(st_ov.iterations, info.iters);
-    stats->matvecs = st_ov.matvecs + info.cnt.matvecs + 3;
-    stats->matvecs_f64 = st_ov.matvecs_f64 + info.cnt.matvecs64 + 3;
-    stats->refinements = st_ov.refinements + info.refinements;
+    stats->iterations = info.iters;
+    stats->matvecs = info.cnt.matvecs + 1 + nsys * n;
+    stats->matvecs_f64 = info.cnt.matvecs64 + 1 + nsys * n;
+    stats->refinements = info.refinements;
     stats->n_shifts = n;
   }
   return solve_rc;

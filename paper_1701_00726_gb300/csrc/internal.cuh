@@ -63,6 +63,8 @@ struct bri_ctx {
   bool have_links = false;
   bool have_clover = false;
   double c_sw = 0.0;
+  // kernel operator of the overlap solvers: BRI_KERNEL_BRILLOUIN or BRI_KERNEL_WILSON
+  int kernel = BRI_KERNEL_BRILLOUIN;
   // Stored off-axis links, structure-of-arrays: FP64 and BF16 [40][9][V]
   // complex, element (nu, e, n) at (nu*9 + e)*V + n; FP32 [40][5][V] pairs of
   // complex (elements 2k, 2k+1 in one 16-byte word, tenth slot padding).  A
@@ -113,6 +115,13 @@ int dirac_bri(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagge
               cudaStream_t s);
 int dirac_wil(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
               cudaStream_t s);
+// The overlap's kernel operator selected on the context (bri_set_kernel):
+// the Brillouin stencil (Eq. def_bril) or the Wilson stencil (Eq. def_wils).
+int dirac_kernel(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
+                 cudaStream_t s);
+// Makes the stencil autotuner's choices for this lattice (every rhs class and
+// precision a solve of precision prec uses) before concurrent work starts.
+int pretune_stencils(bri_ctx* c, int prec);
 
 // Device scratch from a caller-provided block (used by the entry point that
 // allocates nothing); when no arena is set the solvers allocate from the
@@ -124,6 +133,12 @@ struct ScratchArena {
 };
 void set_current_arena(ScratchArena* a);
 ScratchArena* current_arena();
+// Device address of the allocation-free entry point's static scratch array,
+// looked up once per device (with that device current) at set-up time.
+int noalloc_prepare_current_device();
+// Process-wide count of device allocations the library has made (solver
+// workspaces, link and clover storage).
+void note_device_alloc();
 
 // host-side KL coefficients
 int kl_host(int n, int kind, double scale, double* c0, double* w, double* sigma);

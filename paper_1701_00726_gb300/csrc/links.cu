@@ -285,6 +285,7 @@ int launch_build_links(bri_ctx* c, const double* U, double c_sw) {
       set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
       return BRI_ERR_OOM;
     }
+    note_device_alloc();
     return BRI_OK;
   };
   int rc;

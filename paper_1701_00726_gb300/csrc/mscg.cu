@@ -356,9 +356,12 @@ __global__ void k_axpby(int64_t n, double cb, const double* __restrict__ b, doub
     y[i] = cb * b[i] + cz * z[i];
 }
 
+// Reduction grids: blocks per system, at most kMaxPartials partial sums in all
+// (for nsys <= kMaxPartials: blocks * nsys <= kMaxPartials).
+constexpr int kMaxPartials = 2048;
 int grid_for(int64_t n, int nsys) {
   int64_t b = (n + RED_THREADS - 1) / RED_THREADS;
-  int64_t cap = std::max<int64_t>(1, 2048 / std::max(1, nsys));
+  int64_t cap = std::max<int64_t>(1, kMaxPartials / std::max(1, nsys));
   return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
@@ -408,6 +411,7 @@ struct DevBuf {
       set_error(std::string("cudaMallocAsync failed: ") + cudaGetErrorString(e));
       return BRI_ERR_OOM;
     }
+    note_device_alloc();
     return BRI_OK;
   }
   void reset() { release(); }
@@ -492,8 +496,8 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
     dim3 vga(nblk, na);
     for (int j = 0; j < count; ++j) {
       int q;
-      if ((q = dirac_bri(c, t, p, na, m0, 0, oprec, st))) return q;
-      if ((q = dirac_bri(c, q_vec, t, na, m0, 1, oprec, st))) return q;
+      if ((q = dirac_kernel(c, t, p, na, m0, 0, oprec, st))) return q;
+      if ((q = dirac_kernel(c, q_vec, t, na, m0, 1, oprec, st))) return q;
       k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q_vec, part); note_launch();
       k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
       k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (T*)x, part, it0 + j == 0 ? 1 : 0);
@@ -576,8 +580,8 @@ int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X
   cudaStream_t st = c->stream;
   const int64_t n = c->g.V * 24;
   int rc;
-  if ((rc = dirac_bri(c, tmp1, X, nsys, m0, 0, BRI_PREC_F64, st))) return rc;
-  if ((rc = dirac_bri(c, tmp2, tmp1, nsys, m0, 1, BRI_PREC_F64, st))) return rc;
+  if ((rc = dirac_kernel(c, tmp1, X, nsys, m0, 0, BRI_PREC_F64, st))) return rc;
+  if ((rc = dirac_kernel(c, tmp2, tmp1, nsys, m0, 1, BRI_PREC_F64, st))) return rc;
   cnt->matvecs += 2;
   cnt->matvecs64 += 2;
   const int nblk = grid_for(n / 2, nsys);
@@ -648,8 +652,11 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
     DevBuf btmp1, btmp2, bpart, bdsum, bres;
     if ((rc = btmp1.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
     if ((rc = btmp2.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-    const int nblk_r = grid_for(nreal / 2, std::max(nrhs, 32));
-    if ((rc = bpart.alloc(sizeof(double) * nblk_r * std::max(nrhs, 32), st))) return rc;
+    // The partials buffer serves three grids: the nrhs-wide residuals below,
+    // the correction update (up to 32 systems) and the single-system FP64
+    // verification residuals; grid_for caps every one of them at kMaxPartials.
+    const int nblk_r = grid_for(nreal / 2, nrhs);
+    if ((rc = bpart.alloc(sizeof(double) * std::max<int64_t>((int64_t)nblk_r * nrhs, kMaxPartials), st))) return rc;
     if ((rc = bdsum.alloc(sizeof(double) * std::max(nrhs, 32), st))) return rc;
     if ((rc = bres.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
     std::vector<double> bn2(nrhs), rn2((size_t)n * nrhs), tmp(std::max(nrhs, 32));
@@ -720,8 +727,8 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
         if ((rc = bt2.alloc(sizeof(float) * nreal * m, st))) return rc;
         // (FP32 links even when the solve used BF16 ones: the update must be
         // accurate to ~1e-7 of the old residual)
-        if ((rc = dirac_bri(c, bt1.as<float>(), bsol.as<float>(), m, m0, 0, BRI_PREC_F32, st))) return rc;
-        if ((rc = dirac_bri(c, bt2.as<float>(), bt1.as<float>(), m, m0, 1, BRI_PREC_F32, st))) return rc;
+        if ((rc = dirac_kernel(c, bt1.as<float>(), bsol.as<float>(), m, m0, 0, BRI_PREC_F32, st))) return rc;
+        if ((rc = dirac_kernel(c, bt2.as<float>(), bt1.as<float>(), m, m0, 1, BRI_PREC_F32, st))) return rc;
         cnt.matvecs += 2;
         const int nblk_u = grid_for(nreal / 2, m);
         k_correct<<<dim3(nblk_u, m), RED_THREADS, 0, st>>>(nreal, bslot.as<long long>(), bsig.as<double>(),
@@ -860,7 +867,7 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   k_rational<<<dim3(grid_for(nreal, nrhs), nrhs), RED_THREADS, 0, st>>>(nreal, nrhs, n, c0, bw.as<double>(), b, X,
                                                                        bacc.as<double>()); note_launch();
   BRI_LAUNCH_CHECK("k_rational");
-  if ((rc = dirac_bri(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) return rc;
+  if ((rc = dirac_kernel(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) return rc;
   cnt.matvecs += 1;
   cnt.matvecs64 += 1;
   k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), (double*)y); note_launch();

@@ -12,10 +12,14 @@
 // The array is a static __device__ object of this translation unit: every
 // device on which the library is loaded holds it (32 MiB) until the process
 // exits.  Host code must not use its name as a device address; the address is
-// obtained with cudaGetSymbolAddress once per device, on the first call made
-// with that device current.
+// obtained with cudaGetSymbolAddress once per device, with that device
+// current, when bri_build_links runs there (set-up time).  Under CUDA's lazy
+// module loading that lookup is also the moment the array's memory is
+// committed, so a caller whose memory is reserved by its own pool pays for it
+// at set-up, not inside the allocation-free call.
 #include "internal.cuh"
 
+#include <mutex>
 #include <string>
 
 namespace {
@@ -25,6 +29,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
 char* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
 
 // Bytes the FP64 solve needs: the n solution vectors, the n shifted search
 // directions and three work vectors per right-hand side (192 B per site each),
@@ -34,6 +39,29 @@ size_t noalloc_need(int64_t V, int nrhs, int n) {
 }
 
 }  // namespace
+
+namespace bri {
+
+// Looks up (once per device, with that device current) the device address of
+// the static scratch array.  Called from bri_build_links.
+int noalloc_prepare_current_device() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc set-up: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("noalloc set-up: device ordinal out of range");
+    return BRI_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (g_scratch_addr[dev]) return BRI_OK;
+  void* ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc set-up: cudaGetSymbolAddress");
+  g_scratch_addr[dev] = (char*)ptr;
+  return BRI_OK;
+}
+
+}  // namespace bri
 
 using namespace bri;
 
@@ -66,13 +94,18 @@ extern "C" int sign_apply_multishift_noalloc(bri_ctx* c, void* y, const void* x,
     set_error("sign_apply_multishift_noalloc: device ordinal out of range");
     return BRI_ERR_INVALID;
   }
-  if (!g_scratch_addr[dev]) {  // once per device, with that device current
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "sign_apply_multishift_noalloc: cudaGetSymbolAddress");
-    g_scratch_addr[dev] = (char*)ptr;
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    base = g_scratch_addr[dev];
   }
-  ScratchArena arena{g_scratch_addr[dev], kNoallocScratchBytes, 0};
+  if (!base) {  // links built with another device current: set up this one now
+    const int prc = noalloc_prepare_current_device();
+    if (prc) return prc;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    base = g_scratch_addr[dev];
+  }
+  ScratchArena arena{base, kNoallocScratchBytes, 0};
   bri_stats local;
   if (st) local = *st;
   else memset(&local, 0, sizeof(local));

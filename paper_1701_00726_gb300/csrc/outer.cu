@@ -7,13 +7,18 @@
 // Divided by rho, every operator of the cascade has the form
 //   K_j = D_{-rho} r_j(D^dagger D) + (1 + mt/rho),
 // with r_j the Kenney-Laub rational of order j (K_0 uses r = 1: the kernel
-// itself plus the constant, Eq. cascaded_one).  The outer operator K_n is
-// solved with right-preconditioned BiCGstab whose preconditioner is an inexact
-// solve with K_{n_inner} (relative 1e-2), itself preconditioned by an inexact
-// solve with K_0 (Eqs. cascaded_one, cascaded_two); x = solution of
-// K_n x = bt / rho.
+// itself plus the constant, Eq. cascaded_one) and D the context's kernel
+// operator.  Without a cascade (n_inner = 0) K_n is solved by BiCGstab, the
+// paper's outer method.  With the cascade the preconditioner of K_n is an
+// inexact solve with K_{n_inner} (relative 1e-2), itself preconditioned by an
+// inexact solve with K_0 (Eqs. cascaded_one, cascaded_two).  An inexact inner
+// solve is a different operator at every application, so the two outer levels
+// use flexible GMRES (Saad, SIAM J. Sci. Comput. 14 (1993) 461), which keeps
+// the preconditioned directions z_j and stays exact for a varying
+// preconditioner; x = solution of K_n x = bt / rho.
 #include "internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <functional>
@@ -87,6 +92,7 @@ struct Vec {
       set_error("overlap_solve: cudaMallocAsync failed");
       return BRI_ERR_OOM;
     }
+    note_device_alloc();
     return BRI_OK;
   }
 };
@@ -185,6 +191,194 @@ int bicgstab(Ctx& cx, const Op& K, const Op* M, double2* x, const double2* b, do
   return rn <= tol * bn ? BRI_OK : BRI_NOT_CONVERGED;
 }
 
+// Gram-Schmidt helpers of FGMRES: the Krylov basis is one contiguous block
+// V = [j][n] complex.  part[i][blk] = partial <V_i, w> (conj(V_i) w).
+constexpr int MD_BLK = 256;
+__global__ void k_multidot(int64_t n, const double2* __restrict__ V, const double2* __restrict__ w, double2* part) {
+  const double2* v = V + (int64_t)blockIdx.y * n;
+  double re = 0.0, im = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = v[i], b = w[i];
+    re += a.x * b.x + a.y * b.y;
+    im += a.x * b.y - a.y * b.x;
+  }
+  __shared__ double sr[TH / 32], si[TH / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0, q = 0.0;
+    for (int k = 0; k < TH / 32; ++k) {
+      r += sr[k];
+      q += si[k];
+    }
+    part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(r, q);
+  }
+}
+
+constexpr int MAXM = 64;
+struct Coefs {
+  double2 c[MAXM];
+};
+// w += sum_{k<j} c_k V_k
+__global__ void k_multi_axpy(int64_t n, int j, const __grid_constant__ Coefs cf, const double2* __restrict__ V,
+                             double2* w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 acc = w[i];
+    for (int k = 0; k < j; ++k) {
+      const double2 v = V[(int64_t)k * n + i], c = cf.c[k];
+      acc.x += c.x * v.x - c.y * v.y;
+      acc.y += c.x * v.y + c.y * v.x;
+    }
+    w[i] = acc;
+  }
+}
+
+// h[k] = <V_k, w> for k < j (one launch, host sum in a fixed order)
+int multidot(Ctx& cx, const double2* V, int j, const double2* w, std::vector<cplx>& h) {
+  k_multidot<<<dim3(MD_BLK, j), TH, 0, cx.c->stream>>>(cx.n, V, w, cx.part);
+  note_launch();
+  BRI_CUDA(cudaMemcpyAsync(cx.hpart.data(), cx.part, sizeof(double2) * MD_BLK * j, cudaMemcpyDeviceToHost,
+                           cx.c->stream));
+  BRI_CUDA(cudaStreamSynchronize(cx.c->stream));
+  h.assign(j, cplx(0.0, 0.0));
+  for (int k = 0; k < j; ++k) {
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < MD_BLK; ++b) {
+      re += cx.hpart[(size_t)k * MD_BLK + b].x;
+      im += cx.hpart[(size_t)k * MD_BLK + b].y;
+    }
+    h[k] = cplx(re, im);
+  }
+  return BRI_OK;
+}
+
+void multi_axpy(Ctx& cx, const double2* V, int j, const std::vector<cplx>& c, double sign, double2* w) {
+  Coefs cf;
+  for (int k = 0; k < j; ++k) cf.c[k] = make_double2(sign * c[k].real(), sign * c[k].imag());
+  k_multi_axpy<<<NBLK, TH, 0, cx.c->stream>>>(cx.n, j, cf, V, w);
+  note_launch();
+}
+
+// Flexible GMRES(m) for K x = b with a right preconditioner M that may change
+// from one application to the next (an inexact inner solve): the Arnoldi
+// relation K Z_m = V_{m+1} Hbar_m holds with the preconditioned directions
+// z_j = M(v_j) kept, and x = x0 + Z_m y with y minimising
+// ||beta e_1 - Hbar_m y|| (complex Givens rotations).  Orthogonalisation is
+// classical Gram-Schmidt applied twice.  x holds the initial guess.  A cycle
+// ends when the Arnoldi residual estimate reaches tol ||b||; with check_true
+// the true residual b - K x then decides, and the next cycle restarts from x.
+int fgmres(Ctx& cx, const Op& K, const Op* M, double2* x, const double2* b, double tol, int m, int maxit,
+           bool check_true, int* iters, double* relres) {
+  cudaStream_t st = cx.c->stream;
+  m = std::max(1, std::min(m, MAXM - 1));
+  Vec V, Z, w;
+  int rc;
+  if ((rc = V.alloc(cx.n * (m + 1), st))) return rc;
+  if ((rc = Z.alloc(cx.n * m, st))) return rc;
+  if ((rc = w.alloc(cx.n, st))) return rc;
+  const double bn = std::sqrt(cx.dot(b, b).real());
+  if (cx.rc) return cx.rc;
+  *iters = 0;
+  *relres = 0.0;
+  if (bn == 0.0) {
+    cudaMemsetAsync(x, 0, sizeof(double2) * cx.n, st);
+    return BRI_OK;
+  }
+  int it = 0;
+  double rn = 0.0;
+  std::vector<cplx> h, h2, g(m + 1), cs(m), sn(m), y(m);
+  std::vector<std::vector<cplx>> H(m, std::vector<cplx>(m + 1));
+  while (true) {
+    // r0 = b - K x, v_0 = r0 / ||r0||
+    if ((rc = K(w.p, x))) return rc;
+    cx.axpby(1.0, b, -1.0, w.p);
+    rn = std::sqrt(cx.dot(w.p, w.p).real());
+    if (cx.rc) return cx.rc;
+    if (!std::isfinite(rn)) {
+      set_error("overlap_solve: FGMRES met a non-finite residual");
+      return BRI_ERR_NONFINITE;
+    }
+    if (rn <= tol * bn || it >= maxit) break;
+    cx.axpby(1.0 / rn, w.p, 0.0, V.p);
+    std::fill(g.begin(), g.end(), cplx(0.0, 0.0));
+    g[0] = rn;
+    int j = 0;
+    double est = rn;
+    while (j < m && it < maxit) {
+      ++it;
+      double2* vj = V.p + (int64_t)j * cx.n;
+      double2* zj = Z.p + (int64_t)j * cx.n;
+      if (M) {
+        cudaMemsetAsync(zj, 0, sizeof(double2) * cx.n, st);
+        if ((rc = (*M)(zj, vj))) return rc;
+      } else {
+        cx.copy(zj, vj);
+      }
+      if ((rc = K(w.p, zj))) return rc;
+      // two passes of classical Gram-Schmidt against v_0..v_j
+      if ((rc = multidot(cx, V.p, j + 1, w.p, h))) return rc;
+      multi_axpy(cx, V.p, j + 1, h, -1.0, w.p);
+      if ((rc = multidot(cx, V.p, j + 1, w.p, h2))) return rc;
+      multi_axpy(cx, V.p, j + 1, h2, -1.0, w.p);
+      for (int i = 0; i <= j; ++i) h[i] += h2[i];
+      const double hn = std::sqrt(cx.dot(w.p, w.p).real());
+      if (cx.rc) return cx.rc;
+      if (!std::isfinite(hn)) {
+        set_error("overlap_solve: FGMRES met a non-finite basis vector");
+        return BRI_ERR_NONFINITE;
+      }
+      for (int i = 0; i <= j; ++i) H[j][i] = h[i];
+      H[j][j + 1] = hn;
+      if (hn > 0.0) cx.axpby(1.0 / hn, w.p, 0.0, V.p + (int64_t)(j + 1) * cx.n);
+      // the previous rotations on the new column, then the one that zeroes H[j][j+1]
+      for (int i = 0; i < j; ++i) {
+        const cplx a = H[j][i], bb = H[j][i + 1];
+        H[j][i] = cs[i] * a + sn[i] * bb;
+        H[j][i + 1] = -std::conj(sn[i]) * a + cs[i] * bb;
+      }
+      const cplx a = H[j][j];
+      const double r = std::hypot(std::abs(a), hn);
+      if (std::abs(a) == 0.0) {
+        cs[j] = 0.0;
+        sn[j] = 1.0;
+      } else {
+        cs[j] = std::abs(a) / r;
+        sn[j] = (a / std::abs(a)) * hn / r;
+      }
+      H[j][j] = cs[j] * a + sn[j] * hn;
+      H[j][j + 1] = 0.0;
+      g[j + 1] = -std::conj(sn[j]) * g[j];
+      g[j] = cs[j] * g[j];
+      est = std::abs(g[j + 1]);
+      ++j;
+      if (est <= tol * bn || hn == 0.0) break;
+    }
+    // y = R^{-1} g, x += Z y
+    for (int i = j - 1; i >= 0; --i) {
+      cplx v = g[i];
+      for (int k = i + 1; k < j; ++k) v -= H[k][i] * y[k];
+      y[i] = v / H[i][i];
+    }
+    multi_axpy(cx, Z.p, j, y, 1.0, x);
+    if (!check_true && (est <= tol * bn || it >= maxit)) {
+      rn = est;
+      break;
+    }
+  }
+  if (cx.rc) return cx.rc;
+  *iters = it;
+  *relres = rn / bn;
+  return rn <= tol * bn ? BRI_OK : BRI_NOT_CONVERGED;
+}
+
 }  // namespace
 
 int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, int n_inner, int kind, double rho,
@@ -195,20 +389,24 @@ int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, in
   const double k = 1.0 - am / (2.0 * rho);
   const double mt = am / k;
   const double shift = 1.0 + mt / rho;
-  const double inner_tol_sign = std::min(1e-10, tol * 0.1);
+  // Accuracy of the outer operator's sign function: the solution can be ~rho/mt
+  // times larger than the right-hand side, so the rational is applied to
+  // 0.1 tol mt/rho (at most 1e-10, at least 1e-14) for the outer residual to
+  // be meaningful at tol.
+  const double inner_tol_sign = std::max(1e-14, std::min(1e-10, 0.1 * tol * std::min(1.0, mt / rho)));
   Vec part, bt, tmp;
   int rc;
-  if ((rc = part.alloc(NBLK, st))) return rc;
+  if ((rc = part.alloc(std::max(NBLK, MD_BLK * MAXM), st))) return rc;
   if ((rc = bt.alloc(n, st))) return rc;
   if ((rc = tmp.alloc(n, st))) return rc;
-  Ctx cx{c, n, part.p, std::vector<double2>(NBLK)};
+  Ctx cx{c, n, part.p, std::vector<double2>(std::max(NBLK, MD_BLK * MAXM))};
   int matvecs = 0, sign_iters = 0;
 
   // K_j y = D r_j(A) x + shift x  (j = 0: the kernel)
   auto make_K = [&](int order, double sign_tol) -> Op {
     return [=, &matvecs, &sign_iters](double2* y, const double2* xin) -> int {
       if (order == 0) {
-        int r = dirac_bri(c, y, xin, 1, m0, 0, BRI_PREC_F64, st);
+        int r = dirac_kernel(c, y, xin, 1, m0, 0, BRI_PREC_F64, st);
         if (r) return r;
         k_caxpby<<<NBLK, TH, 0, st>>>(n, make_double2(shift, 0.0), xin, make_double2(1.0, 0.0), y);
         note_launch();
@@ -248,7 +446,7 @@ int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, in
   if (n_inner > 0) {
     const Op K_inner = make_K(n_inner, 1e-6);
     const Op K_kernel = make_K(0, 0.0);
-    // level 0: inexact solve with the kernel operator
+    // level 0: inexact solve with the kernel operator (a fixed operator, BiCGstab)
     const Op M0 = [&](double2* y, const double2* r) -> int {
       int it = 0;
       double rr = 0.0;
@@ -256,15 +454,15 @@ int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, in
       inner_it_total += it;
       return q < 0 ? q : BRI_OK;
     };
-    // level 1: inexact solve with K_{n_inner}, preconditioned by level 0
+    // level 1: inexact solve with K_{n_inner}, flexibly preconditioned by level 0
     const Op M1 = [&](double2* y, const double2* r) -> int {
       int it = 0;
       double rr = 0.0;
-      int q = bicgstab(cx, K_inner, &M0, y, r, 1e-2, 50, &it, &rr);
+      int q = fgmres(cx, K_inner, &M0, y, r, 1e-2, 32, 32, false, &it, &rr);
       inner_it_total += it;
       return q < 0 ? q : BRI_OK;
     };
-    rc = bicgstab(cx, K_outer, &M1, x, bt.p, tol, maxiter, &outer_it, &relres);
+    rc = fgmres(cx, K_outer, &M1, x, bt.p, tol, 24, maxiter, true, &outer_it, &relres);
   } else {
     rc = bicgstab(cx, K_outer, nullptr, x, bt.p, tol, maxiter, &outer_it, &relres);
   }
@@ -276,7 +474,7 @@ int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, in
     cx.axpby(1.0, bt.p, -1.0, tmp.p);
     relres = std::sqrt(cx.dot(tmp.p, tmp.p).real() / cx.dot(bt.p, bt.p).real());
     if (cx.rc) return cx.rc;
-    if (rc == BRI_OK && relres > 10 * tol) rc = BRI_NOT_CONVERGED;
+    if (rc == BRI_OK && relres > tol) rc = BRI_NOT_CONVERGED;
   }
   cudaStreamSynchronize(st);
   if (st_out) {

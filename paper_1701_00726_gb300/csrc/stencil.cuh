@@ -4,6 +4,8 @@
 #include "internal.cuh"
 #include "cplx.cuh"
 
+#include <mutex>
+
 namespace bri {
 
 template <typename R> struct Spinor {
@@ -139,6 +141,7 @@ struct StencilConfig {
 };
 bool tune_lookup(const char* key, StencilConfig* out);
 void tune_store(const char* key, const StencilConfig& cf);
+std::mutex& tune_mutex();
 
 // Host-side launchers (one translation unit per precision).
 template <typename R, typename LS>

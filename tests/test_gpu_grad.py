@@ -26,7 +26,8 @@ def _traceless_hermitian(shape, seed):
 
 @pytest.mark.parametrize("am,anti", [(0.0, False), (0.3, True)])
 def test_grad_vs_oracle(am, anti):
-    dims = (4, 2, 3, 2)
+    """Ragged 6x5x4x3 lattice (every extent >= 3, so +d and -d hops land on different sites)."""
+    dims = (6, 5, 4, 3)
     n = 6
     u = sf.gauge_field(dims, 91)
     eta = sf.gaussian_source(dims, 2, 92, normalize=True)

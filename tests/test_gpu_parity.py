@@ -6,6 +6,8 @@ lattice 2^4 makes every neighbour wrap.  Tolerances: FP64 1e-12 relative
 mantissa: each link element carries a relative rounding error up to 2^-9,
 and the 80 hop terms add with random signs), solver results 1e-10.
 """
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -188,8 +190,8 @@ def test_bri_apply_full_size_sampled():
 
 @pytest.mark.parametrize("prec", [PREC_F32, PREC_F32_BF16])
 def test_mixed_order16_true_residuals(prec):
-    """KL order 16 (smallest shift 2.3e-3), stout-smeared field, c_SW = 1: every shift's FP64
-    true residual reaches the requested 1e-10 and D_ov agrees with the FP64 GPU path."""
+    """KL order 16 (smallest shift 2.3e-3), stout-smeared 8^4 field, c_SW = 1: every shift's FP64
+    true residual reaches the requested 1e-10 (FP32 and BF16 links in the first phase)."""
     dims = (8, 8, 8, 8)
     u = sf.gauge_field(dims, 1, 0.1, 3)
     x = sf.gaussian_source(dims, 3, 1001)
@@ -198,8 +200,73 @@ def test_mixed_order16_true_residuals(prec):
     y, st = lat.overlap_apply(xt, n=16, rho=1.0, tol=1e-10, prec=prec, want_true_residual=True)
     assert st["converged"]
     assert st["max_true_residual"] <= 1e-10
-    y64, st64 = lat.overlap_apply(xt, n=16, rho=1.0, tol=1e-12, prec=PREC_F64)
-    assert relerr(y.cpu().numpy(), y64.cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [PREC_F32, PREC_F32_BF16])
+def test_mixed_order16_vs_oracle(prec):
+    """The benchmark's Kenney-Laub order 16 in mixed precision against the FP64 oracle on the
+    ragged lattice (stout-smeared field, c_SW = 1): within 1e-10."""
+    dims = RAGGED
+    u = sf.gauge_field(dims, 1, 0.1, 3)
+    x = sf.gaussian_source(dims, 1, 1011)
+    lat = _lattice(dims, u, 1.0)
+    y, st = lat.overlap_apply(torch.from_numpy(x).cuda(), n=16, rho=1.0, tol=1e-11, prec=prec)
+    assert st["converged"]
+    assert relerr(y.cpu().numpy(), _oracle_order16_ragged()) < 1e-10
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_order16_ragged():
+    u = sf.gauge_field(RAGGED, 1, 0.1, 3)
+    x = sf.gaussian_source(RAGGED, 1, 1011)
+    want, _ = overlap.overlap_apply(dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0), x, 1.0, 16, 1e-13)
+    return want
+
+
+def test_mixed_many_rhs():
+    """48 right-hand sides (more than the 32-system correction batches and the reduction grid's
+    per-system split) on 8^4: mixed result against the FP64 path, every shift at the requested
+    true residual."""
+    dims = (8, 8, 8, 8)
+    u = sf.gauge_field(dims, 2, 0.1, 3)
+    x = torch.from_numpy(sf.gaussian_source(dims, 48, 1012)).cuda()
+    lat = _lattice(dims, u, 1.0)
+    y, st = lat.overlap_apply(x, n=4, rho=1.0, tol=1e-11, prec=PREC_F32, want_true_residual=True)
+    assert st["converged"]
+    assert st["max_true_residual"] <= 1e-11
+    y64, _ = lat.overlap_apply(x, n=4, rho=1.0, tol=1e-13, prec=PREC_F64)
+    assert relerr(y.cpu().numpy(), y64.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol,bound", [(PREC_F64, 1e-13, 1e-12), (PREC_F32, 1e-11, 1e-10)])
+def test_overlap_wilson_kernel(prec, tol, bound):
+    """D_ov with the Wilson kernel (Eq. def_wils inside Eq. def_over), c_SW = 1, massive
+    traditional form and the sign function of the upper-diagonal family, against the oracle."""
+    dims = RAGGED
+    u = sf.gauge_field(dims, 8, 0.1, 3)
+    x = sf.gaussian_source(dims, 2, 1013)
+    lat = _lattice(dims, u, 1.0)
+    lat.set_kernel("wil")
+    xt = torch.from_numpy(x).cuda()
+    want, swant1 = _oracle_wilson_overlap()
+    y, st = lat.overlap_apply(xt, n=8, rho=1.0, am=0.1, tol=tol, prec=prec)
+    assert st["converged"]
+    assert relerr(y.cpu().numpy(), want) < bound
+    s1, _ = lat.sign_apply(xt, n=4, rho=1.0, tol=tol, prec=prec, kind=1)
+    assert relerr(s1.cpu().numpy(), swant1) < bound
+    lat.set_kernel("bri")
+    yb, _ = lat.overlap_apply(xt, n=8, rho=1.0, am=0.1, tol=tol, prec=prec)
+    assert relerr(yb.cpu().numpy(), want) > 1e-3  # the selector really switches the kernel
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_wilson_overlap():
+    u = sf.gauge_field(RAGGED, 8, 0.1, 3)
+    x = sf.gaussian_source(RAGGED, 2, 1013)
+    kern = dirac.DiracOperator(u, "wil", m0=-1.0, c_sw=1.0)
+    want, _ = overlap.overlap_apply(kern, x, 1.0, 8, 1e-13, am=0.1)
+    swant1, _ = overlap.sign_apply(kern, x, 4, 1e-13, kind=1)
+    return want, swant1
 
 
 @pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "0,64,1", "1,64,1", "2,128,1", "2,64,1", "0,128,2", "0,128,4"])

@@ -27,12 +27,31 @@ def test_noalloc_matches_allocating_entry_point():
     assert st_ref["converged"]
     refn = ref.cpu().numpy()
     out = torch.empty_like(x)
+    allocs0 = Lattice.device_allocations()
     for _ in range(2):  # the static scratch keeps the previous call's contents
         y, st = lat.sign_apply_noalloc(x, n=8, rho=1.0, tol=1e-12, out=out)
         assert st["converged"]
         got = y.cpu().numpy()
         assert np.abs(got - refn).max() <= 1e-12 * np.abs(refn).max()
+    # the defining property: no device allocation by the library in those calls
+    assert Lattice.device_allocations() == allocs0
     big = torch.zeros((64,) + tuple(x.shape[1:]), dtype=torch.complex128, device="cuda")
     with pytest.raises(BriError, match="static scratch"):
         lat.sign_apply_noalloc(big, n=8)
+    lat.close()
+
+
+def test_noalloc_documented_size_limit():
+    """8^4 with one right-hand side fits up to KL order 19; order 20 is refused."""
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims)
+    lat.build_links(torch.from_numpy(sf.gauge_field(dims, 2)).cuda(), 0.0)
+    x = torch.from_numpy(sf.gaussian_source(dims, 1, 1002)).cuda()
+    out = torch.empty_like(x)
+    allocs0 = Lattice.device_allocations()
+    _, st = lat.sign_apply_noalloc(x, n=19, rho=1.0, tol=1e-10, out=out)
+    assert st["converged"]
+    assert Lattice.device_allocations() == allocs0
+    with pytest.raises(BriError, match="static scratch"):
+        lat.sign_apply_noalloc(x, n=20, out=out)
     lat.close()
