@@ -10,10 +10,15 @@ application of D.  Inputs (stout-smeared synthetic SU(3) field, complex
 Gaussian sources) are resident in HBM when the timed region starts.
 
 Printed (rank 0, one JSON line): D_ov applies per second over all ranks, the
-stencil's roofline figures measured with CUDA events inside the timed region,
-an end-to-end figure through the same C ABI call with host buffers, and the
-FP64 CPU oracle timed on a bounded sample.  ``--impl reference`` times the
-oracle alone.
+stencil's roofline figures measured with CUDA events inside the timed region
+(against FMA and copy peaks measured on this GPU), an end-to-end figure
+through the same C ABI call with host buffers, and the FP64 CPU oracle timed
+on a bounded sample on all host cores and on one.  After the timed region, on
+rank 0: the FP64 true residual of every shift of the timed step (an untimed
+repeat that reproduces the timed output bit for bit), the single-rhs stencil
+in FP32, BF16-link and FP64 form against its HBM and FP64 rooflines, and the
+plain FP64 GPU solve with the mixed-over-FP64 ratio.  ``--impl reference``
+times the oracle alone.
 
 Multi-GPU (torchrun): every rank runs an independent replica (own gauge field
 and sources), there is no data-path collective; the per-step time is the
@@ -51,8 +56,15 @@ CLOVER_BYTES = 72 * 4
 SPINOR_BYTES = 2 * 96
 # algorithmic flops of the Brillouin matvec per site and right-hand side (App. C)
 FLOPS_PER_SITE = 30168
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock
-FP32_LANES = 152 * 128
+# algorithmic bytes of one FP64 stencil launch per site: links 40 x 144, clover 72 doubles,
+# and per site and rhs one spinor read and one written (2 x 192 B)
+F64_LINK_CLOVER_BYTES = 40 * 144 + 72 * 8
+F64_SPINOR_BYTES = 2 * 192
+# oracle sample lattices (one D_ov of the workload's settings per process): the
+# cpu_baseline of the GPU arm, and the smaller per-step sample of the reference
+# arm, which runs warmup + steps rounds and has to end within a few minutes
+CPU_SAMPLE = (4, 4, 4, 4)
+REF_SAMPLE = (4, 4, 2, 2)
 
 
 def parse():
@@ -65,8 +77,10 @@ def parse():
     ap.add_argument("--links", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fp64-compare", action="store_true",
-                    help="also time one plain FP64 D_ov (1 rhs) outside the timed region")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain FP64 D_ov (1 rhs) timed after the timed region")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the post-timed checks (true residuals, single-rhs stencils, FMA probes)")
     ap.add_argument("--stencil-probe", default=None, metavar="LX,LY,LZ,LT",
                     help="profiling helper: only launch the FP32 Brillouin stencil on this lattice and print "
                          "its CUDA-event time (used for the ncu captures under profiles/)")
@@ -222,6 +236,70 @@ def oracle_sample(dims, n, tol, nrhs=1):
     return time.perf_counter() - t0, dims[0] * dims[1] * dims[2] * dims[3] * nrhs
 
 
+def _oracle_task(dims):
+    return oracle_sample(tuple(dims), KL_ORDER, TOL)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: one single-threaded oracle D_ov per
+    worker process, the workers started with 'spawn' (never forked from a
+    process that holds a CUDA context)."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        self.cores = cores
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        self.pool = mp.get_context("spawn").Pool(cores)
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        self.pool.map(int, range(cores))  # workers up before any timing
+
+    def step(self, dims):
+        """One oracle D_ov on the lattice dims per core, concurrently; (wall seconds, applications)."""
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_task, [dims] * self.cores)
+        return time.perf_counter() - t0, len(res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def sample_fraction(dims):
+    """One application on the lattice dims as a fraction of one 24^3x48 application (by volume)."""
+    vs = dims[0] * dims[1] * dims[2] * dims[3]
+    return vs / float(DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3])
+
+
+def cpu_baseline_measure():
+    """cpu_baseline: the oracle on all host cores (one concurrent round) and on one core."""
+    cores = host_cores()
+    dt1, _ = oracle_sample(CPU_SAMPLE, KL_ORDER, TOL)
+    pool = OraclePool(cores)
+    try:
+        dtn, napp = pool.step(CPU_SAMPLE)
+    finally:
+        pool.close()
+    frac = sample_fraction(CPU_SAMPLE)
+    return {"value": napp * frac / dtn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "one_core": {"value": frac / dt1, "cores": 1, "seconds": round(dt1, 2)},
+            "sample": (f"FP64 numpy oracle, one D_ov (KL order {KL_ORDER}, tol {TOL:g}, c_SW {C_SW:g}, stout field) on "
+                       f"{'x'.join(map(str, CPU_SAMPLE))} per process, {cores} processes at once ({dtn:.1f} s) and "
+                       f"one alone ({dt1:.1f} s); applications scaled by volume to 24^3x48")}
+
+
 def workload_config(nrhs, world, inner):
     """The `config` of both arms' JSON lines (the same workload; `inner` names the arithmetic)."""
     return {"workload": f"24^3x48 massless overlap apply, {nrhs} rhs per step, stout 3x0.1, c_SW=1, "
@@ -231,27 +309,34 @@ def workload_config(nrhs, world, inner):
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step is one concurrent round of
+    oracle D_ov applications on CPU_SAMPLE, one per host core."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    sample = (4, 4, 4, 4)
-    vfull = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
-    for _ in range(args.warmup):
-        oracle_sample(sample, KL_ORDER, TOL)
-    t = 0.0
-    for _ in range(args.steps):
-        dt, vs = oracle_sample(sample, KL_ORDER, TOL)
-        t += dt * vfull / vs  # seconds one full-volume application would take
-    value = args.steps / t  # D_ov applications per second
-    desc = (f"FP64 numpy oracle: one D_ov (KL order {KL_ORDER}, tol {TOL:g}, c_SW {C_SW:g}) per step on a 4^4 "
-            f"lattice, time scaled by volume to 24^3x48; a step of the workload ({args.nrhs} rhs) is "
-            f"{args.nrhs} such applications")
+    cores = host_cores()
+    pool = OraclePool(cores)
+    try:
+        for _ in range(args.warmup):
+            pool.step(REF_SAMPLE)
+        t = 0.0
+        napp = 0
+        for _ in range(args.steps):
+            dt, k = pool.step(REF_SAMPLE)
+            t += dt
+            napp += k
+    finally:
+        pool.close()
+    value = napp * sample_fraction(REF_SAMPLE) / t  # 24^3x48-equivalent D_ov applications per second
+    desc = (f"FP64 numpy oracle: per step one D_ov (KL order {KL_ORDER}, tol {TOL:g}, c_SW {C_SW:g}, stout field) "
+            f"on {'x'.join(map(str, REF_SAMPLE))} in each of {cores} processes at once; applications scaled by "
+            f"volume to 24^3x48")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t * args.nrhs / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.nrhs, world, "fp64 numpy oracle on the host (volume-scaled 4^4 sample)"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": workload_config(args.nrhs, world, "fp64 numpy oracle on the host cores (volume-scaled sample)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -301,7 +386,6 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    import numpy as np
     import torch
 
     import synthetic_fields as sf
@@ -360,13 +444,20 @@ def main():
 
     # roofline of the dominant kernel (the FP32 Brillouin stencil): the
     # attainable time of its launches is max(bytes / HBM peak, flops / FP32
-    # peak) with algorithmic bytes and flops; the larger term names the bound.
+    # FMA peak) with algorithmic bytes and flops; the larger term names the
+    # bound.  Both peaks are measured on this GPU (copy bandwidth from
+    # MEASURED_PEAKS.json, FMA rate by the library's probe kernel).
+    from paper_1701_00726_gb300 import _lib
     peak, peak_src = measured_peak()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_scalar, _ = _lib.fma_probe(1, stream.cuda_stream)
+    fp32_paired, _ = _lib.fma_probe(2, stream.cuda_stream)
+    fp64_peak, _ = _lib.fma_probe(0, stream.cuda_stream)
+    fp32_peak = max(fp32_scalar, fp32_paired)
+    clock_mhz = (clk or {}).get("sm_mhz") or 2070.0
     alg_bytes = nlaunch * vol * (LINK_BYTES[prec] + CLOVER_BYTES) + units * SPINOR_BYTES
     alg_flops = units * FLOPS_PER_SITE
     ksec = kms / 1e3
-    clock_mhz = (clk or {}).get("sm_mhz") or 2070.0
-    fp32_peak = FP32_LANES * 2 * clock_mhz * 1e6 / 1e12  # TFLOP/s
     t_hbm = alg_bytes / (peak * 1e9)
     t_alu = alg_flops / (fp32_peak * 1e12)
     traffic = stencil_traffic()
@@ -378,11 +469,13 @@ def main():
               "alg_flops_per_launch": int(alg_flops / max(nlaunch, 1)),
               "stencil_share_of_step": round(ksec / elapsed, 4) if world == 1 else None,
               "traffic": stencil_traffic_per_launch(traffic, vol, nlaunch, units, prec)}
+    probe_src = (f"measured: bri_fma_probe on {sms} SMs (FP32 FMA {fp32_scalar:.1f}, paired FP32 FMA "
+                 f"{fp32_paired:.1f} TFLOP/s; nominal {sms} x 128 lanes x 2 x {clock_mhz:.0f} MHz = "
+                 f"{sms * 128 * 2 * clock_mhz / 1e6:.1f})")
     if t_alu >= t_hbm:
         achieved = alg_flops / ksec / 1e12 if ksec > 0 else 0.0
         roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (median SM clock in the timed region)",
+                "frac": round(achieved / fp32_peak, 4), "peak_source": probe_src,
                 "hbm_GBps_alg": round(alg_bytes / ksec / 1e9, 1) if ksec > 0 else 0.0}
     else:
         achieved = alg_bytes / ksec / 1e9 if ksec > 0 else 0.0
@@ -391,14 +484,16 @@ def main():
                 "alu_TFLOPs_alg": round(alg_flops / ksec / 1e12, 2) if ksec > 0 else 0.0}
     roof.update(common)
 
-    # end to end through the same C ABI call with host buffers
+    # end to end through the same C ABI call with host buffers (pinned), both
+    # copies inside the timed region
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(x_host).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
+        e_steps = max(1, min(args.steps, 5))
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(e_steps):
             xd = xh.to("cuda", non_blocking=True)
             yd, _ = lat.overlap_apply(xd, n=KL_ORDER, rho=RHO, tol=TOL, prec=prec)
             yh.copy_(yd, non_blocking=True)
@@ -409,27 +504,69 @@ def main():
             t = torch.tensor([te], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             te = float(t.item())
-        e2e = {"value": applies / te, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 16),
-               "d2h_bytes_per_step": int(yh.numel() * 16)}
+        e2e = {"value": e_steps * nrhs * world / te, "unit": UNIT, "steps": e_steps,
+               "h2d_bytes_per_step": int(xh.numel() * 16), "d2h_bytes_per_step": int(yh.numel() * 16)}
 
-    fp64 = None
-    if args.fp64_compare and rank == 0:
-        xs = x[:1].contiguous()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, st64 = lat.overlap_apply(xs, n=KL_ORDER, rho=RHO, tol=TOL, prec=PREC_F64)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        fp64 = {"applies_per_s_1rhs": 1.0 / t64, "seconds": t64, "iterations": st64["iterations"],
-                "mixed_over_fp64": value / world / (1.0 / t64)}
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # (1) the timed step's accuracy: an untimed repeat with FP64 true residuals
+        # of every shift; the solver is deterministic, so its output must equal the
+        # timed output bit for bit, and the residuals are those of the timed step
+        y_chk, st_chk = lat.overlap_apply(x, n=KL_ORDER, rho=RHO, tol=TOL, prec=prec, want_true_residual=True)
+        extras["accuracy"] = {"max_true_residual": st_chk["max_true_residual"], "tol": TOL,
+                              "shift_residual_max": max(st_chk["shift_residual"]),
+                              "repeat_bitwise_equal_to_timed": bool(torch.equal(y_chk, y))}
+        del y_chk
+        # (2) the single-rhs stencil against its rooflines (CUDA events, 20 launches)
+        x1 = x[:1].to(torch.complex64).contiguous()
+        y1 = torch.empty_like(x1)
+
+        def stencil_ms(xx, yy, bf16):
+            lat.bri_apply(xx, -RHO, bf16_links=bf16, out=yy)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ea.record(stream)
+            for _ in range(20):
+                lat.bri_apply(xx, -RHO, bf16_links=bf16, out=yy)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            return ea.elapsed_time(eb) / 20
+
+        one = {}
+        for name, bf16, lb in (("fp32_links", False, LINK_BYTES[1]), ("bf16_links", True, LINK_BYTES[2])):
+            ms = stencil_ms(x1, y1, bf16)
+            byt = vol * (lb + CLOVER_BYTES + SPINOR_BYTES)
+            one[name] = {"ms": round(ms, 4), "alg_bytes": byt, "alg_GBps": round(byt / ms / 1e6, 1),
+                         "hbm_frac": round(byt / ms / 1e6 / peak, 4),
+                         "alu_frac": round(vol * FLOPS_PER_SITE / ms / 1e9 / fp32_peak, 4)}
+        one["hbm_peak_GBps"] = peak
+        one["hbm_peak_source"] = peak_src
+        x64 = x[:1].contiguous()
+        y64 = torch.empty_like(x64)
+        ms64 = stencil_ms(x64, y64, False)
+        one["fp64"] = {"ms": round(ms64, 3), "alg_TFLOPs": round(vol * FLOPS_PER_SITE / ms64 / 1e9, 3),
+                       "fp64_peak_TFLOPs": round(fp64_peak, 3),
+                       "alu_frac": round(vol * FLOPS_PER_SITE / ms64 / 1e9 / fp64_peak, 4),
+                       "alg_GBps": round(vol * (F64_LINK_CLOVER_BYTES + F64_SPINOR_BYTES) / ms64 / 1e6, 1)}
+        extras["bri_apply_1rhs"] = one
+        extras["fma_peaks_TFLOPs"] = {"fp64": round(fp64_peak, 3), "fp32": round(fp32_scalar, 2),
+                                      "fp32_paired": round(fp32_paired, 2), "sms": sms}
+        del x1, y1, x64, y64
+        # (3) the plain FP64 GPU solve (one rhs) and the mixed-over-FP64 ratio
+        if not args.no_fp64:
+            xs = x[:1].contiguous()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st64 = lat.overlap_apply(xs, n=KL_ORDER, rho=RHO, tol=TOL, prec=PREC_F64)
+            torch.cuda.synchronize()
+            t64 = time.perf_counter() - t0
+            extras["fp64_gpu"] = {"applies_per_s": 1.0 / t64, "seconds_per_apply": round(t64, 3), "rhs": 1,
+                                  "iterations": st64["iterations"], "converged": st64["converged"],
+                                  "mixed_over_fp64": round(value / world / (1.0 / t64), 3)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = (4, 4, 4, 4)
-        dt, vs = oracle_sample(sample, KL_ORDER, TOL)
-        cpu = {"value": 1.0 / (dt * vol / vs), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 numpy-oracle D_ov on 4^4 (same generator, KL order {KL_ORDER}, tol {TOL:g}, "
-                         f"c_SW {C_SW:g}, 1 rhs), {dt:.1f} s, scaled by volume to 24^3x48"}
+        cpu = cpu_baseline_measure()
 
     if rank == 0:
         last = stats[-1]
@@ -444,8 +581,7 @@ def main():
                        "matvecs_f64": last["matvecs_f64"], "refinements": last["refinements"],
                        "phase_seconds": [round(v, 4) for v in last["phase_seconds"]]},
         }
-        if fp64 is not None:
-            line["fp64_gpu"] = fp64
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

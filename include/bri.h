@@ -185,10 +185,11 @@ int overlap_solve(bri_ctx* ctx, void* x, const void* b, int nrhs, int n_outer, i
  * ([V][4][3][3] complex128), with the conventions dL = Re<g_psi, dpsi> and
  * dL = Re sum tr(g_U^dagger dU) (those of PyTorch's complex autograd).  The
  * derivative runs through the multi-shift solves (x_i for psi and z_i for
- * D^dagger eta, same shifts) and the path-averaged link construction (App. C).
- * The clover term is not differentiated: the links must have been built with
- * c_sw = 0 (BRI_ERR_INVALID otherwise).  prec as for overlap_apply (solves);
- * the force and link back-propagation run in FP64. */
+ * D^dagger eta, same shifts; g_psi reuses the z_i) and the path-averaged link
+ * construction (App. C) -- for the Wilson kernel the thin links directly --
+ * and, when the links were built with c_sw != 0, through the clover term (its
+ * four-leaf field strength).  prec as for overlap_apply (solves); the force
+ * and link back-propagation run in FP64. */
 int overlap_grad(bri_ctx* ctx, void* g_psi, void* g_U, const void* eta, const void* psi, int nrhs, int n,
                  int kind, double rho, double am, double scale, double tol, int prec, bri_stats* st);
 
@@ -223,6 +224,62 @@ int sign_apply_multishift_noalloc(bri_ctx* ctx, void* y, const void* x, int nrhs
  * processed since the previous read, then resets the counters. */
 int bri_profile_enable(bri_ctx* ctx, int enable);
 int bri_profile_read(bri_ctx* ctx, int op, int prec, long long* launches, double* ms, double* site_rhs);
+
+/* Quality diagnostics of the massless overlap operator D = D_ov of
+ * Kenney-Laub order n (Sec. 5): for each of the nrhs vectors eta (device
+ * complex128 [nrhs][V][4][3]) writes the normality defect
+ * ||(D D^dagger - D^dagger D) eta|| (Sec. 5.1) and the Ginsparg-Wilson defect
+ * ||(D gamma5 + gamma5 D - (1/rho) D gamma5 D) eta|| (Sec. 5.2, Eq.
+ * ginswils_one) into the host arrays normality[nrhs] and gw[nrhs]
+ * (absolute 2-norms; the paper normalises eta to 1).  Uses D^dagger =
+ * gamma5 D gamma5: two overlap applications to 2 nrhs vectors.  The context's
+ * kernel, kind, rho, tol and prec as for overlap_apply; st may be NULL. */
+int overlap_quality(bri_ctx* ctx, const void* eta, int nrhs, int n, int kind, double rho, double tol, int prec,
+                    double* normality, double* gw, bri_stats* st);
+
+/* Locality of the massless overlap operator (Sec. 5.3): zeta = D_ov eta for
+ * nrhs sources eta (device complex128 [nrhs][V][4][3]) supported on the site
+ * src, and per source the sum of |zeta(x)| (spin-colour 2-norm) over the sites
+ * x with Euclidean distance |x - src|^2 = b (minimal periodic image) into the
+ * host array profile[nrhs][nbins], and the number of such sites into counts[nbins]
+ * (distances with |x - src|^2 >= nbins are left out).  The profile is summed
+ * with atomic additions, so its last bits may differ between runs. */
+int overlap_locality(bri_ctx* ctx, const void* eta, int nrhs, int src, int n, int kind, double rho, double tol,
+                     int prec, int nbins, double* profile, int* counts, bri_stats* st);
+
+/* Nested Kenney-Laub iterate D^(k) of the shifted kernel (Sec. 4.1):
+ * X = D_K(m0 = -rho), Y_1 = X r_{n1}(X^dagger X), Y_j = Y_{j-1} r_{nj}(Y_{j-1}^dagger Y_{j-1})
+ * with the diagonal rationals of orders orders[0..levels-1] (host array), and
+ * y = D^(k) x = rho (x + Y_k x), k = levels (1..4).  Level 1 is overlap_apply
+ * of order n1; each further level is a multi-shift solve whose operator
+ * applications are solves of the level below (FP64 throughout, relative
+ * residual tol at every level).  By the nesting of the principal Pade maps,
+ * orders {1, 1} give the same operator as order 4 (g_3 o g_3 = g_9 = f_44).
+ * x, y: device complex128 [nrhs][V][4][3]; st may be NULL. */
+int overlap_nested_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int levels, const int* orders, double rho,
+                         double tol, bri_stats* st);
+
+/* Free-field quark dispersion relations (Sec. 2, App. A): for npts spatial
+ * momenta p (host, [npts][3], lattice units) and quark masses am (host,
+ * [npts]) writes the energies aE (host, [npts]) of the free Wilson
+ * (kernel = BRI_KERNEL_WILSON) or Brillouin (BRI_KERNEL_BRILLOUIN) operator,
+ * or, with overlap != 0, of the overlap operator built on that kernel with
+ * the exact sign function at parameter rho.  E is the smallest positive zero
+ * of the free propagator's denominator after p4 -> iE (the transcendental
+ * equations of App. A), one GPU thread per point: scanned from E = 0 in steps
+ * of 2e-3 up to E = 8, then bisected to full FP64 precision; NaN where no zero
+ * lies below E = 8.  Allocates a small device buffer; synchronises stream. */
+int bri_dispersion(int kernel, int overlap, double rho, int npts, const double* p, const double* am, double* energy,
+                   void* stream);
+
+/* Measured fused-multiply-add throughput of this GPU, the ALU roofline of the
+ * stencils (App. C counts the matvec in flops; it runs on CUDA cores).  kind:
+ * 0 = FP64 FMA, 1 = FP32 FMA, 2 = paired FP32 FMA (fma.rn.f32x2).  A grid of
+ * 8 blocks per SM, each thread advancing eight independent FMA chains, timed
+ * with CUDA events on stream (best of three launches after one warm-up).
+ * Writes TFLOP/s (2 flops per FMA) and the kernel milliseconds; allocates a
+ * small output buffer; synchronises the stream. */
+int bri_fma_probe(int kind, void* stream, double* tflops, double* ms);
 
 /* Process-wide number of CUDA kernels this library has launched so far. */
 long long bri_kernel_launches(void);

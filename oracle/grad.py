@@ -2,7 +2,8 @@
 
 D_m = (1 - am/(2 rho)) D_ov + am with D_ov = rho (1 + D r(D^dagger D)),
 r(s) = c0 + sum_i w_i / (s + sigma_i) (Eqs. def_over, KLnn_parfrac,
-def_mass_traditional), D the Brillouin kernel at m0 = -rho without clover term.
+def_mass_traditional), D the Brillouin or Wilson kernel at m0 = -rho, with
+or without the clover term (Eqs. def_bril, def_wils).
 The real-gradient convention is dL = Re <g, d psi> and
 dL = Re sum_{n,mu} tr(G_mu(n)^dagger dU_mu(n)) (the convention of PyTorch's
 complex autograd).  The paper gives the ingredients (Sec. 9: with a
@@ -19,6 +20,15 @@ written out here is:
   link U at position j of a path product A U B receives A^dagger G_W B^dagger
   (a backward step U^dagger receives B G_W^dagger A).  This module enumerates
   every path literally, independently of the recursion used on the GPU.
+
+The clover term C(n) = -(c_SW/2) sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(n),
+F = P[(Q - Q^dagger)/(8i)] (P: traceless part, Q: the sum of the four leaves
+around n in the (mu, nu) plane), contributes Re<u, dC v>, whose gradient with
+respect to F_{mu nu}(n) is G_F = -(c_SW/2) sum_t (sigma_{mu nu} u(n))_t v_t(n)^dagger
+(colour outer product, spin summed).  P is self-adjoint under Re tr(A^dagger B),
+and Re tr(G^dagger (dQ - dQ^dagger)/(8i)) = Re tr(G_Q^dagger dQ) with
+G_Q = (i/8) (P G_F + (P G_F)^dagger); G_Q then flows into the links of every
+leaf with the same rule as for a path product.
 """
 from __future__ import annotations
 
@@ -27,7 +37,7 @@ import math
 
 import numpy as np
 
-from .conventions import all_offsets, dag, shift_by
+from .conventions import all_offsets, dag, gammas, shift_by
 from .dirac import DiracOperator, gamma5
 from .kl import kl_coeffs
 from .links import apply_time_bc
@@ -100,9 +110,54 @@ def link_gradient_from_transporters(u_bc, gw):
     return gu
 
 
-def overlap_grad(u, eta, psi, rho, n, tol, am=0.0, kind=0, antiperiodic_t=False):
+def _clover_leaves(mu, nu):
+    """The four leaves at n in the (mu, nu) plane, each as its four factors
+    (direction, daggered, site offset a e_mu + b e_nu), in product order."""
+    def at(a, b):
+        return tuple(a * (k == mu) + b * (k == nu) for k in range(4))
+    return [
+        [(mu, False, at(0, 0)), (nu, False, at(1, 0)), (mu, True, at(0, 1)), (nu, True, at(0, 0))],
+        [(nu, False, at(0, 0)), (mu, True, at(-1, 1)), (nu, True, at(-1, 0)), (mu, False, at(-1, 0))],
+        [(mu, True, at(-1, 0)), (nu, True, at(-1, -1)), (mu, False, at(-1, -1)), (nu, False, at(0, -1))],
+        [(nu, True, at(0, -1)), (mu, False, at(0, -1)), (nu, False, at(1, -1)), (mu, True, at(0, 0))],
+    ]
+
+
+def clover_link_gradient(u_bc, c_sw, pairs):
+    """G_U[t,z,y,x,mu,3,3] of sum_p weight_p Re<u_p, dC v_p> (clover term only)."""
+    g, _ = gammas()
+    site_shape = u_bc.shape[:4]
+    gu = np.zeros(site_shape + (4, 3, 3), dtype=np.complex128)
+    eye = np.broadcast_to(np.eye(3, dtype=np.complex128), site_shape + (3, 3))
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            sig = 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+            gf = np.zeros(site_shape + (3, 3), dtype=np.complex128)
+            for u, v, wt in pairs:
+                su = np.einsum("ts,...sa->...ta", sig, u[0])
+                gf += -0.5 * c_sw * wt * np.einsum("...ta,...tb->...ab", su, v[0].conj())
+            gp = gf - np.trace(gf, axis1=-2, axis2=-1)[..., None, None] * np.eye(3) / 3.0
+            gq = 0.125j * (gp + dag(gp))
+            for leaf in _clover_leaves(mu, nu):
+                mats = []
+                for d, is_dag, at in leaf:
+                    link = shift_by(u_bc[..., d, :, :], at)
+                    mats.append(dag(link) if is_dag else link)
+                for j, (d, is_dag, at) in enumerate(leaf):
+                    a = eye
+                    for mm in mats[:j]:
+                        a = a @ mm
+                    b = eye
+                    for mm in mats[j + 1:]:
+                        b = b @ mm
+                    contrib = b @ dag(gq) @ a if is_dag else dag(a) @ gq @ dag(b)
+                    gu[..., d, :, :] += _shift_back(contrib, at)
+    return gu
+
+
+def overlap_grad(u, eta, psi, rho, n, tol, am=0.0, kind=0, antiperiodic_t=False, c_sw=0.0, kernel="bri"):
     """(g_psi, G_U) for L = Re <eta, D_m psi> summed over the right-hand sides."""
-    kern = DiracOperator(u, "bri", m0=-rho, antiperiodic_t=antiperiodic_t)
+    kern = DiracOperator(u, kernel, m0=-rho, c_sw=c_sw, antiperiodic_t=antiperiodic_t)
     g_psi, _ = overlap_apply(kern, gamma5(eta), rho, n, tol, am=am, kind=kind)
     g_psi = gamma5(g_psi)
     c0, w, sig = kl_coeffs(n, kind)
@@ -122,12 +177,14 @@ def overlap_grad(u, eta, psi, rho, n, tol, am=0.0, kind=0, antiperiodic_t=False)
     gw = transporter_gradient(kern, pairs)
     u_bc = apply_time_bc(u, antiperiodic_t)
     gu = link_gradient_from_transporters(u_bc, gw)
+    if c_sw != 0.0:
+        gu = gu + clover_link_gradient(u_bc, c_sw, pairs)
     if antiperiodic_t:
         gu[-1, :, :, :, 3] *= -1.0
     return g_psi, gu
 
 
-def loss(u, eta, psi, rho, n, tol, am=0.0, kind=0, antiperiodic_t=False):
-    kern = DiracOperator(u, "bri", m0=-rho, antiperiodic_t=antiperiodic_t)
+def loss(u, eta, psi, rho, n, tol, am=0.0, kind=0, antiperiodic_t=False, c_sw=0.0, kernel="bri"):
+    kern = DiracOperator(u, kernel, m0=-rho, c_sw=c_sw, antiperiodic_t=antiperiodic_t)
     y, _ = overlap_apply(kern, psi, rho, n, tol, am=am, kind=kind)
     return float(np.vdot(eta.ravel(), y.ravel()).real)

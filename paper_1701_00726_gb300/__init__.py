@@ -16,9 +16,10 @@ import ctypes
 
 from . import _lib
 from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KERNEL_BRILLOUIN, KERNEL_WILSON, KL_DIAGONAL, KL_UPPER,
-                   PREC_F32, PREC_F32_BF16, PREC_F64, BriError, BriStats, kl_coeffs)
+                   PREC_F32, PREC_F32_BF16, PREC_F64, BriError, BriStats, dispersion, kl_coeffs)
 
-__all__ = ["Lattice", "overlap", "OverlapFunction", "overlap_apply_batch", "kl_coeffs", "BriError", "BriStats",
+__all__ = ["Lattice", "overlap", "OverlapFunction", "overlap_apply_batch", "kl_coeffs", "dispersion", "BriError",
+           "BriStats",
            "PREC_F64", "PREC_F32", "PREC_F32_BF16", "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T", "KERNEL_BRILLOUIN",
            "KERNEL_WILSON"]
 
@@ -174,7 +175,8 @@ class Lattice:
     def overlap_grad(self, eta, psi, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL, scale=1.0,
                      maxiter=0):
         """Adjoint of overlap_apply for L = sum_r Re<eta_r, D_m psi_r>: returns (g_psi, g_U, stats),
-        g_U with the shape [Lt, Lz, Ly, Lx, 4, 3, 3] of the gauge field (links built with c_sw = 0)."""
+        g_U with the shape [Lt, Lz, Ly, Lx, 4, 3, 3] of the gauge field (through the off-axis links
+        or, for the Wilson kernel, the thin links, and the clover term when c_sw != 0)."""
         torch = _torch()
         nrhs = self._spinor(psi, (torch.complex128,))
         if self._spinor(eta, (torch.complex128,)) != nrhs:
@@ -204,6 +206,52 @@ class Lattice:
                                                     ctypes.c_void_p(x.data_ptr()), nrhs, int(n), int(kind),
                                                     float(rho), float(scale), float(tol), ctypes.byref(st))
         _lib.check(rc, "sign_apply_multishift_noalloc")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return y, d
+
+    def quality(self, eta, n, rho=1.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL):
+        """Normality and Ginsparg-Wilson defects ||(D D^+ - D^+ D) eta||, ||(D g5 + g5 D - D g5 D / rho) eta||
+        of the massless overlap of order n, per source (Sec. 5).  Returns (normality, gw, stats)."""
+        torch = _torch()
+        nrhs = self._spinor(eta, (torch.complex128,))
+        nm = (ctypes.c_double * nrhs)()
+        gw = (ctypes.c_double * nrhs)()
+        st = self._solver_stats(False, 0)
+        rc = self.lib.overlap_quality(self._h, ctypes.c_void_p(eta.data_ptr()), nrhs, int(n), int(kind), float(rho),
+                                      float(tol), int(prec), nm, gw, ctypes.byref(st))
+        _lib.check(rc, "overlap_quality")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        return list(nm), list(gw), d
+
+    def locality(self, eta, src, n, nbins, rho=1.0, tol=1e-12, prec=PREC_F64, kind=KL_DIAGONAL):
+        """Sec. 5.3: per source, the sum of |D_ov eta (x)| over sites with |x - src|^2 = b, b < nbins,
+        and the number of such sites.  ``src`` is a site index.  Returns (profile[nrhs][nbins], counts, stats)."""
+        torch = _torch()
+        nrhs = self._spinor(eta, (torch.complex128,))
+        prof = (ctypes.c_double * (nrhs * nbins))()
+        cnt = (ctypes.c_int * nbins)()
+        st = self._solver_stats(False, 0)
+        rc = self.lib.overlap_locality(self._h, ctypes.c_void_p(eta.data_ptr()), nrhs, int(src), int(n), int(kind),
+                                       float(rho), float(tol), int(prec), int(nbins), prof, cnt, ctypes.byref(st))
+        _lib.check(rc, "overlap_locality")
+        d = st.as_dict()
+        d["converged"] = rc == 0
+        p = [list(prof[r * nbins:(r + 1) * nbins]) for r in range(nrhs)]
+        return p, list(cnt), d
+
+    def nested_apply(self, x, orders, rho=1.0, tol=1e-12, out=None):
+        """D^(k) x = rho (x + Y_k x) with the nested Kenney-Laub iterates of the given orders (Sec. 4.1)."""
+        torch = _torch()
+        nrhs = self._spinor(x, (torch.complex128,))
+        y = torch.empty_like(x) if out is None else out
+        orders = [int(v) for v in orders]
+        arr = (ctypes.c_int * len(orders))(*orders)
+        st = self._solver_stats(False, 0)
+        rc = self.lib.overlap_nested_apply(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                           nrhs, len(orders), arr, float(rho), float(tol), ctypes.byref(st))
+        _lib.check(rc, "overlap_nested_apply")
         d = st.as_dict()
         d["converged"] = rc == 0
         return y, d
@@ -266,8 +314,8 @@ class OverlapFunction:
 
             class _Overlap(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, psi, u, lattice, n, rho, am, tol, prec):
-                    lattice.build_links(u.detach().contiguous(), 0.0)
+                def forward(ctx, psi, u, lattice, n, rho, am, tol, prec, c_sw):
+                    lattice.build_links(u.detach().contiguous(), c_sw)
                     y, _ = lattice.overlap_apply(psi.detach().contiguous(), n, rho=rho, am=am, tol=tol, prec=prec)
                     ctx.save_for_backward(psi.detach())
                     ctx.cfg = (lattice, n, rho, am, tol, prec)
@@ -279,12 +327,13 @@ class OverlapFunction:
                     lattice, n, rho, am, tol, prec = ctx.cfg
                     g_psi, g_u, _ = lattice.overlap_grad(grad_y.contiguous(), psi, n, rho=rho, am=am, tol=tol,
                                                          prec=prec)
-                    return g_psi, g_u, None, None, None, None, None, None
+                    return g_psi, g_u, None, None, None, None, None, None, None
 
             cls._fn = _Overlap
         return cls._fn
 
 
-def overlap(psi, u, lattice, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64):
-    """Differentiable D_m psi = (1 - am/(2 rho)) D_ov psi + am psi (links rebuilt from ``u``, c_sw = 0)."""
-    return OverlapFunction.get().apply(psi, u, lattice, n, rho, am, tol, prec)
+def overlap(psi, u, lattice, n, rho=1.0, am=0.0, tol=1e-12, prec=PREC_F64, c_sw=0.0):
+    """Differentiable D_m psi = (1 - am/(2 rho)) D_ov psi + am psi, with the lattice's kernel
+    (links and clover term rebuilt from ``u`` with coefficient ``c_sw``)."""
+    return OverlapFunction.get().apply(psi, u, lattice, n, rho, am, tol, prec, c_sw)

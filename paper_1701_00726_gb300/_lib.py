@@ -96,6 +96,22 @@ _SIGS = {
     "bri_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "bri_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "overlap_quality": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(BriStats)]),
+    "overlap_locality": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(BriStats)]),
+    "overlap_nested_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                            ctypes.c_double, ctypes.POINTER(BriStats)]),
+    "bri_dispersion": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "bri_fma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "bri_kernel_launches": (ctypes.c_longlong, []),
     "bri_device_allocations": (ctypes.c_longlong, []),
     "bri_last_error": (ctypes.c_char_p, []),
@@ -125,6 +141,29 @@ def check(rc, what):
     if rc < 0:
         raise BriError(f"{what} failed ({rc}): {load().bri_last_error().decode()}")
     return rc
+
+
+def dispersion(momenta, masses, kernel=KERNEL_BRILLOUIN, overlap=False, rho=1.0, stream=0):
+    """Free-field energies aE for spatial momenta [(p1, p2, p3), ...] and masses am (Sec. 2, App. A)."""
+    lib = load()
+    n = len(masses)
+    if n == 0 or len(momenta) != n:
+        raise BriError("dispersion: need one mass per momentum")
+    p = (ctypes.c_double * (3 * n))(*[float(c) for q in momenta for c in q])
+    m = (ctypes.c_double * n)(*[float(v) for v in masses])
+    e = (ctypes.c_double * n)()
+    check(lib.bri_dispersion(int(kernel), int(bool(overlap)), float(rho), n, p, m, e, ctypes.c_void_p(stream)),
+          "bri_dispersion")
+    return list(e)
+
+
+def fma_probe(kind, stream=0):
+    """(TFLOP/s, ms) of the FMA-throughput probe: kind 0 FP64, 1 FP32, 2 paired FP32."""
+    lib = load()
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    check(lib.bri_fma_probe(int(kind), ctypes.c_void_p(stream), ctypes.byref(tf), ctypes.byref(ms)), "bri_fma_probe")
+    return tf.value, ms.value
 
 
 def kl_coeffs(n, kind=KL_DIAGONAL, scale=1.0):

@@ -331,14 +331,6 @@ int overlap_grad(bri_ctx* c, void* g_psi, void* g_U, const void* eta, const void
     set_error("overlap_grad: null, aliased or misaligned eta / g_U");
     return BRI_ERR_INVALID;
   }
-  if (c->have_clover) {
-    set_error("overlap_grad: the clover term is not differentiated; build the links with c_sw = 0");
-    return BRI_ERR_INVALID;
-  }
-  if (c->kernel != BRI_KERNEL_BRILLOUIN) {
-    set_error("overlap_grad: only the Brillouin kernel is differentiated");
-    return BRI_ERR_INVALID;
-  }
   if (!std::isfinite(am) || am >= 2.0 * rho) {
     set_error("overlap_grad: the traditional massive form needs am < 2 rho");
     return BRI_ERR_INVALID;

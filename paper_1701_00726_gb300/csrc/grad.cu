@@ -13,7 +13,10 @@
 // G_W = u(n) (M_d v(n+d))^dagger (kernel k_force); the gradients are then
 // pushed back through the path average (App. C) by reversing the last-step
 // recursion W_d = (1/k) sum_mu W_{d - s e_mu} U_step level by level, as
-// gathers (no atomics).  The clover term is not differentiated (c_SW = 0).
+// gathers (no atomics).  With the Wilson kernel (Eq. def_wils) the transporters
+// are the thin links themselves, so only the one-hop terms exist and the
+// gradients go straight to the links.  The clover term adds, per site and
+// plane, the gradient of its leaf sum (kernels k_clover_force, k_clover_links).
 #include "hops.cuh"
 
 namespace bri {
@@ -25,13 +28,20 @@ struct PairList {
   double w[512];
 };
 
-// G_W[idx](n) += sum_p w_p u_p(n) (M_d v_p(n+d))^dagger for the 80 hops d.
-// blockIdx.y = stored offset j (0..39), blockIdx.z = 0 for +d, 1 for -d.
+// Stored offsets (0..39) a force launch covers: all 40 for the Brillouin
+// kernel, the four one-hop ones for the Wilson kernel.
+struct OffsetList {
+  int count;
+  int j[40];
+};
+
+// G_W[idx](n) += sum_p w_p u_p(n) (M_d v_p(n+d))^dagger for the hops d.
+// blockIdx.y = entry of the offset list, blockIdx.z = 0 for +d, 1 for -d.
 __global__ void __launch_bounds__(128) k_force(Geom g, const PairList* __restrict__ pl, int npair, double2* GW,
-                                              const __grid_constant__ HopTable<double> H) {
+                                              const __grid_constant__ HopTable<double> H, OffsetList ol) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
-  const int j = blockIdx.y, opp = blockIdx.z;
+  const int j = ol.j[blockIdx.y], opp = blockIdx.z;
   int m = 0;
   {
     int r = n;
@@ -213,6 +223,178 @@ __global__ void k_zero(int64_t n, double2* p) {
     p[i] = make_double2(0.0, 0.0);
 }
 
+// ------------------------------------------------------------------ clover term
+// C(n) = -(c_SW/2) sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(n), F = P[(Q - Q^+)/(8i)].
+// Re<u, dC v> has the gradient G_F = -(c_SW/2) sum_{t,s} sigma_{ts} O_{st} with
+// the colour outer products O_{st} = u_s(n) v_t(n)^dagger, and
+// G_Q = (i/8) (P G_F + (P G_F)^dagger) with respect to the leaf sum Q.  In the
+// chiral basis sigma_{mu nu} is block diagonal: sigma_12 = -diag(s3, s3),
+// sigma_13 = diag(s2, s2), sigma_23 = -diag(s1, s1), sigma_j4 = diag(s_j, -s_j),
+// so only the four outer products within one chirality block enter, through
+//   B_1 = O_{10} + O_{01},  B_2 = i (O_{01} - O_{10}),  B_3 = O_{00} - O_{11}
+// (spins of the block renumbered 0, 1); the upper block enters every plane with
+// the sign +1, the lower block with -1 in the (j, 4) planes.  One launch per
+// chirality block (blk), each adding its part of G_Q into GQ = [6][9][V], the
+// planes ordered (01, 02, 03, 12, 13, 23).
+__global__ void __launch_bounds__(128) k_clover_force(Geom g, const PairList* __restrict__ pl, int npair, int blk,
+                                                     double c_sw, double2* GQ) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.V) return;
+  C<double> O[2][2][3][3];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) O[s][t][a][b] = C<double>{0, 0};
+  for (int p = 0; p < npair; ++p) {
+    const double2* up = reinterpret_cast<const double2*>(pl->u[p]) + (int64_t)n * 12 + 6 * blk;
+    const double2* vp = reinterpret_cast<const double2*>(pl->v[p]) + (int64_t)n * 12 + 6 * blk;
+    const double wp = pl->w[p];
+    C<double> u[2][3], v[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double2 x = up[s * 3 + a], y = vp[s * 3 + a];
+        u[s][a] = C<double>{wp * x.x, wp * x.y};
+        v[s][a] = C<double>{y.x, y.y};
+      }
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) cfma_cj(O[s][t][a][b], v[t][b], u[s][a]);  // u_sa conj(v_tb)
+  }
+  const double pre = -0.5 * c_sw;
+  const double lo = blk == 0 ? 1.0 : -1.0;  // sign of this block in the (j, 4) planes
+  // plane -> (Pauli index l, sign): 01: (3, -1), 02: (2, +1), 03: (1, lo), 12: (1, -1), 13: (2, lo), 23: (3, lo)
+  const int lidx[6] = {3, 2, 1, 1, 2, 3};
+  const double sgn[6] = {-1.0, 1.0, lo, -1.0, lo, lo};
+#pragma unroll 1
+  for (int pi = 0; pi < 6; ++pi) {
+    C<double> F[3][3];
+    const int l = lidx[pi];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        C<double> v;
+        if (l == 1) {
+          v = O[1][0][a][b] + O[0][1][a][b];
+        } else if (l == 2) {
+          const C<double> d = O[0][1][a][b] - O[1][0][a][b];
+          v = C<double>{-d.im, d.re};
+        } else {
+          v = O[0][0][a][b] - O[1][1][a][b];
+        }
+        F[a][b] = (pre * sgn[pi]) * v;
+      }
+    const C<double> tr = F[0][0] + F[1][1] + F[2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a][a] = F[a][a] - (1.0 / 3.0) * tr;
+    // G_Q = (i/8) (F + F^dagger)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const C<double> h = F[a][b] + conj(F[b][a]);
+        double2* q = GQ + ((int64_t)pi * 9 + a * 3 + b) * g.V + n;
+        double2 cur = *q;
+        cur.x += -h.im / 8.0;
+        cur.y += h.re / 8.0;
+        *q = cur;
+      }
+  }
+}
+
+// The four leaves of a plane (mu, nu) at n, each as four factors in product
+// order: {role (0: U_mu, 1: U_nu), daggered, a, b} for the link at n + a e_mu + b e_nu
+// (the leaves of the clover construction); passed to the kernel by value.
+struct LeafTable {
+  int f[4][4][4];
+};
+constexpr LeafTable kLeaves = {{
+    {{0, 0, 0, 0}, {1, 0, 1, 0}, {0, 1, 0, 1}, {1, 1, 0, 0}},
+    {{1, 0, 0, 0}, {0, 1, -1, 1}, {1, 1, -1, 0}, {0, 0, -1, 0}},
+    {{0, 1, -1, 0}, {1, 1, -1, -1}, {0, 0, -1, -1}, {1, 0, 0, -1}},
+    {{1, 1, 0, -1}, {0, 0, 0, -1}, {1, 0, 1, -1}, {0, 1, 0, 0}},
+}};
+
+__device__ __forceinline__ M3<double> leaf_factor(const Geom& g, const double2* __restrict__ U64, int n, int mu,
+                                                  int nu, const int f[4]) {
+  int d[4] = {0, 0, 0, 0};
+  d[mu] += f[2];
+  d[nu] += f[3];
+  const int dir = f[0] == 0 ? mu : nu;
+  const M3<double> m = ldm(U64 + (int64_t)dir * 9 * g.V, g.V, site_shift(g, n, d));
+  return f[1] ? adj(m) : m;
+}
+
+// G_U_rho(m) += sum over the clover leaves containing U_rho(m): a forward
+// factor of the leaf A U B receives A^dagger G_Q B^dagger, a daggered one
+// (A U^dagger B) receives B G_Q^dagger A (G_Q at the leaf's base site n).
+__global__ void k_clover_links(Geom g, const double2* __restrict__ U64, const double2* __restrict__ GQ, double2* GU,
+                               const __grid_constant__ LeafTable kLeaf) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rho = blockIdx.y;
+  if (m >= g.V) return;
+  M3<double> acc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc.m[a][b] = C<double>{0, 0};
+  int pi = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = mu + 1; nu < 4; ++nu, ++pi) {
+      if (mu != rho && nu != rho) continue;
+      for (int lf = 0; lf < 4; ++lf)
+        for (int j = 0; j < 4; ++j) {
+          const int* fj = kLeaf.f[lf][j];
+          if ((fj[0] == 0 ? mu : nu) != rho) continue;
+          int back[4] = {0, 0, 0, 0};
+          back[mu] -= fj[2];
+          back[nu] -= fj[3];
+          const int n = site_shift(g, m, back);  // base site of the leaf
+          M3<double> A, B;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              A.m[a][b] = C<double>{a == b ? 1.0 : 0.0, 0};
+              B.m[a][b] = A.m[a][b];
+            }
+          for (int k = 0; k < j; ++k) A = mmul(A, leaf_factor(g, U64, n, mu, nu, kLeaf.f[lf][k]));
+          for (int k = j + 1; k < 4; ++k) B = mmul(B, leaf_factor(g, U64, n, mu, nu, kLeaf.f[lf][k]));
+          const M3<double> gq = ldm(GQ + (int64_t)pi * 9 * g.V, g.V, n);
+          madd(acc, fj[1] ? mmul(mmul(B, adj(gq)), A) : mmul(mmul(adj(A), gq), adj(B)));
+        }
+    }
+  addm(GU + (int64_t)rho * 9 * g.V, g.V, m, acc, 1.0);
+}
+
+// Hop table of the Wilson kernel in the Brillouin table's form: the one-hop
+// offsets carry M_{+-mu} = -1/2 (1 -+ gamma_mu), every other offset zero.
+const HopTable<double>& wilson_hop_table() {
+  static const HopTable<double> t = [] {
+    HopTable<double> h;
+    fill_hops(h);
+    for (int j = 0; j < 40; ++j) {
+      int k = 0;
+      for (int mu = 0; mu < 4; ++mu) k += h.site_d[j][mu] != 0;
+      h.a[j] = k == 1 ? -0.5 : 0.0;
+      for (int mu = 0; mu < 4; ++mu) h.cs[j][mu] = k == 1 ? 0.5 * h.site_d[j][mu] : 0.0;
+    }
+    return h;
+  }();
+  return t;
+}
+
 struct Buf {
   void* p = nullptr;
   cudaStream_t s = nullptr;
@@ -270,7 +452,7 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   Buf bb, bX, bDX, by;
   if ((rc = bb.alloc(sizeof(double) * nreal * nsys, st))) return rc;
   BRI_CUDA(cudaMemcpyAsync(bb.as<double>(), psi, sizeof(double) * nreal * nrhs, cudaMemcpyDeviceToDevice, st));
-  if ((rc = dirac_bri(c, bb.as<double>() + nreal * nrhs, eta, nrhs, m0, 1, BRI_PREC_F64, st))) return rc;
+  if ((rc = dirac_kernel(c, bb.as<double>() + nreal * nrhs, eta, nrhs, m0, 1, BRI_PREC_F64, st))) return rc;
   std::vector<double> sig_all((size_t)nsys * n);
   for (int s = 0; s < nsys; ++s)
     for (int k = 0; k < n; ++k) sig_all[(size_t)s * n + k] = sig[k];
@@ -297,13 +479,26 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   k_axpby_real<<<1024, 256, 0, st>>>(nreal * nrhs, kfac + am, eta, kfac, g_psi);
   note_launch();
   if ((rc = bDX.alloc(sizeof(double) * nreal * nsys * n, st))) return rc;
-  if ((rc = dirac_bri(c, bDX.as<double>(), X, nsys * n, m0, 0, BRI_PREC_F64, st))) return rc;
+  if ((rc = dirac_kernel(c, bDX.as<double>(), X, nsys * n, m0, 0, BRI_PREC_F64, st))) return rc;
   BRI_LAUNCH_CHECK("overlap_grad solves");
 
   // transporter gradients from all (u, v, weight) pairs
-  Buf bGW, bpl;
+  const bool wilson = c->kernel == BRI_KERNEL_WILSON;
+  const HopTable<double>& htab = wilson ? wilson_hop_table() : hop_table<double>();
+  OffsetList ol;
+  ol.count = 0;
+  for (int j = 0; j < 40; ++j) {
+    int k = 0;
+    for (int mu = 0; mu < 4; ++mu) k += htab.site_d[j][mu] != 0;
+    if (!wilson || k == 1) ol.j[ol.count++] = j;
+  }
+  Buf bGW, bpl, bGQ;
   if ((rc = bGW.alloc(sizeof(double2) * 81 * 9 * V, st))) return rc;
   k_zero<<<2048, 256, 0, st>>>(81 * 9 * V, bGW.as<double2>()); note_launch();
+  if (c->have_clover) {
+    if ((rc = bGQ.alloc(sizeof(double2) * 6 * 9 * V, st))) return rc;
+    k_zero<<<512, 256, 0, st>>>(6 * 9 * V, bGQ.as<double2>()); note_launch();
+  }
   if ((rc = bpl.alloc(sizeof(PairList), st))) return rc;
   const int per_rhs = 1 + 2 * n;
   const int rhs_per_chunk = std::max(1, 512 / per_rhs);
@@ -329,18 +524,27 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
       }
     }
     BRI_CUDA(cudaMemcpyAsync(bpl.as<PairList>(), &pl, sizeof(PairList), cudaMemcpyHostToDevice, st));
-    dim3 grid(blocks_for(V, 128), 40, 2);
-    k_force<<<grid, 128, 0, st>>>(g, bpl.as<PairList>(), np, bGW.as<double2>(), hop_table<double>()); note_launch();
+    dim3 grid(blocks_for(V, 128), ol.count, 2);
+    k_force<<<grid, 128, 0, st>>>(g, bpl.as<PairList>(), np, bGW.as<double2>(), htab, ol); note_launch();
+    if (c->have_clover)
+      for (int blk = 0; blk < 2; ++blk) {
+        k_clover_force<<<blocks_for(V, 128), 128, 0, st>>>(g, bpl.as<PairList>(), np, blk, c->c_sw,
+                                                           bGQ.as<double2>());
+        note_launch();
+      }
     BRI_CUDA(cudaStreamSynchronize(st));  // the pair list buffer is reused
   }
 
-  // back through the path average to the thin links
+  // back through the path average to the thin links (the Wilson kernel's
+  // transporters are the links: one-hop level only)
   Buf bT, bGU;
-  if ((rc = bT.alloc(sizeof(double2) * 81 * 9 * V, st))) return rc;
-  if ((rc = build_transporters(c, bT.as<double2>()))) return rc;
+  if (!wilson) {
+    if ((rc = bT.alloc(sizeof(double2) * 81 * 9 * V, st))) return rc;
+    if ((rc = build_transporters(c, bT.as<double2>()))) return rc;
+  }
   if ((rc = bGU.alloc(sizeof(double2) * 36 * V, st))) return rc;
   k_zero<<<512, 256, 0, st>>>(36 * V, bGU.as<double2>()); note_launch();
-  for (int k = 4; k >= 2; --k) {
+  for (int k = 4; k >= 2 && !wilson; --k) {
     const LevelList lst = level_list(k), lower = level_list(k - 1);
     k_rev_links<<<dim3(blocks_for(V, 128), 4), 128, 0, st>>>(g, lst, k, bT.as<double2>(), bGW.as<double2>(),
                                                             bGU.as<double2>()); note_launch();
@@ -348,6 +552,11 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
                                                                              bGW.as<double2>()); note_launch();
   }
   k_rev_level1<<<dim3(blocks_for(V, 128), 4), 128, 0, st>>>(g, bGW.as<double2>(), bGU.as<double2>()); note_launch();
+  if (c->have_clover) {
+    k_clover_links<<<dim3(blocks_for(V, 128), 4), 128, 0, st>>>(g, c->U64, bGQ.as<double2>(), bGU.as<double2>(),
+                                                               kLeaves);
+    note_launch();
+  }
   k_links_out<<<blocks_for(V, 128), 128, 0, st>>>(g, bGU.as<double2>(), (double2*)g_U,
                                                   (c->flags & BRI_ANTIPERIODIC_T) ? 1 : 0); note_launch();
   BRI_LAUNCH_CHECK("overlap_grad backward");

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <cstring>
+#include <functional>
 #include <string>
 
 #include "../../include/bri.h"
@@ -143,6 +144,14 @@ void note_device_alloc();
 // host-side KL coefficients
 int kl_host(int n, int kind, double scale, double* c0, double* w, double* sigma);
 
+// A gamma5-hermitian operator in place of the context's kernel for the FP64
+// solvers (the nested Kenney-Laub iterates of Sec. 4.1 solve on Y^dagger Y with
+// Y itself an overlap-type operator): y = K x (dagger = 0) or K^dagger x for
+// nsys systems of V*12 complex128 each, on the context stream.
+struct KernelOp {
+  std::function<int(double2* y, const double2* x, int nsys, int dagger)> apply;
+};
+
 // solvers
 struct Counters {
   int matvecs = 0, matvecs64 = 0;
@@ -154,14 +163,14 @@ struct SolveInfo {
 };
 // (A + sigma_k) X_k = b_s for all shifts k < n, systems s < nsys: X = [n][nsys][V*24] FP64.
 int solve_shifts(bri_ctx* c, const double* b, int nsys, int n, const double* sig, double m0, double tol, int prec,
-                 int maxiter, double* X, SolveInfo& info);
+                 int maxiter, double* X, SolveInfo& info, const KernelOp* op = nullptr);
 int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta, const double* psi, int nrhs, int n,
                       int kind, double rho, double am, double scale, double tol, int prec, bri_stats* stats);
 int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, int n_inner, int kind, double rho,
                        double am, int complete, double tol, int prec, int maxiter, bri_stats* st_out);
 int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho,
                double scale, double tol, int prec, double out_scale, double b_coeff,
-               bri_stats* st);
+               bri_stats* st, const KernelOp* op = nullptr);
 
 // profiling brackets (no-ops unless enabled on the context)
 int prof_begin(bri_ctx* c, cudaStream_t s, cudaEvent_t* a);

@@ -443,7 +443,7 @@ template <> int op_prec<float>(int prec) { return prec == BRI_PREC_F32_BF16 ? BR
 template <typename R>
 int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, const double* sig, const R* b, R* x,
                      double tol, int maxiter, int* iters_out, Counters* cnt, const double* tols,
-                     double* lam_out = nullptr) {
+                     double* lam_out = nullptr, const KernelOp* op = nullptr) {
   using T = typename P2<R>::T;
   cudaStream_t st = c->stream;
   const int64_t n2 = c->g.V * 12;  // complex pairs per system
@@ -496,8 +496,13 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
     dim3 vga(nblk, na);
     for (int j = 0; j < count; ++j) {
       int q;
-      if ((q = dirac_kernel(c, t, p, na, m0, 0, oprec, st))) return q;
-      if ((q = dirac_kernel(c, q_vec, t, na, m0, 1, oprec, st))) return q;
+      if (op) {  // an FP64 operator given by the caller (R = double)
+        if ((q = op->apply((double2*)t, (const double2*)p, na, 0))) return q;
+        if ((q = op->apply((double2*)q_vec, (const double2*)t, na, 1))) return q;
+      } else {
+        if ((q = dirac_kernel(c, t, p, na, m0, 0, oprec, st))) return q;
+        if ((q = dirac_kernel(c, q_vec, t, na, m0, 1, oprec, st))) return q;
+      }
       k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q_vec, part); note_launch();
       k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
       k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (T*)x, part, it0 + j == 0 ? 1 : 0);
@@ -510,7 +515,7 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
   // Blocks after the first are captured once per active-prefix size into a CUDA
   // graph and replayed (fewer launch gaps on small lattices).  Not while the
   // stencils are being profiled, and not on the legacy default stream.
-  const bool graphs = graphs_enabled() && !c->prof_on && st != nullptr;
+  const bool graphs = graphs_enabled() && !c->prof_on && st != nullptr && op == nullptr;
   cudaGraphExec_t gexec = nullptr;
   int g_nact = -1;
   long long g_launches = 0;
@@ -576,12 +581,18 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
 
 // ||b - (A + sigma) X||^2 per system for one shift (FP64 operator); res may be null.
 int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X, double sigma, double* res,
-               double* tmp1, double* tmp2, double* part, double* dsum, double* hsum, Counters* cnt) {
+               double* tmp1, double* tmp2, double* part, double* dsum, double* hsum, Counters* cnt,
+               const KernelOp* op = nullptr) {
   cudaStream_t st = c->stream;
   const int64_t n = c->g.V * 24;
   int rc;
-  if ((rc = dirac_kernel(c, tmp1, X, nsys, m0, 0, BRI_PREC_F64, st))) return rc;
-  if ((rc = dirac_kernel(c, tmp2, tmp1, nsys, m0, 1, BRI_PREC_F64, st))) return rc;
+  if (op) {
+    if ((rc = op->apply((double2*)tmp1, (const double2*)X, nsys, 0))) return rc;
+    if ((rc = op->apply((double2*)tmp2, (const double2*)tmp1, nsys, 1))) return rc;
+  } else {
+    if ((rc = dirac_kernel(c, tmp1, X, nsys, m0, 0, BRI_PREC_F64, st))) return rc;
+    if ((rc = dirac_kernel(c, tmp2, tmp1, nsys, m0, 1, BRI_PREC_F64, st))) return rc;
+  }
   cnt->matvecs += 2;
   cnt->matvecs64 += 2;
   const int nblk = grid_for(n / 2, nsys);
@@ -599,7 +610,7 @@ int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X
 // X = [n][nsys][V*24] FP64; FP64 multi-shift CG or the mixed scheme above.
 
 int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig, double m0, double tol,
-                 int prec, int maxiter, double* X, SolveInfo& info) {
+                 int prec, int maxiter, double* X, SolveInfo& info, const KernelOp* op) {
   cudaStream_t st = c->stream;
   const int64_t nreal = c->g.V * 24;
   int rc = BRI_OK;
@@ -621,9 +632,13 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
     tmark = t1;
   };
   int solve_rc = BRI_OK;
+  if (op && prec != BRI_PREC_F64) {
+    set_error("multi-shift solve: an operator given by the caller needs FP64");
+    return BRI_ERR_INVALID;
+  }
   if (prec == BRI_PREC_F64) {
     solve_rc = multishift_solve<double>(c, prec, m0, nrhs, n, sig_all.data(), b, X, tol, maxiter, &iters, &cnt,
-                                        nullptr);
+                                        nullptr, nullptr, op);
     if (solve_rc < 0) return solve_rc;
     lap(0);
   } else if (prec == BRI_PREC_F32 || prec == BRI_PREC_F32_BF16) {
@@ -808,7 +823,7 @@ struct StreamScope {
 };
 
 int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho, double scale,
-               double tol, int prec, double out_scale, double b_coeff, bri_stats* stats) {
+               double tol, int prec, double out_scale, double b_coeff, bri_stats* stats, const KernelOp* op) {
   StreamScope scope(c);
   auto t0 = std::chrono::steady_clock::now();
   configure_pool_once();
@@ -826,7 +841,7 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   if ((rc = bX.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
   double* X = bX.as<double>();
   SolveInfo info;
-  int solve_rc = solve_shifts(c, b, nrhs, n, sig, m0, tol, prec, maxiter, X, info);
+  int solve_rc = solve_shifts(c, b, nrhs, n, sig, m0, tol, prec, maxiter, X, info, op);
   if (solve_rc < 0) return solve_rc;
   Counters& cnt = info.cnt;
   const int iters = info.iters, refinements = info.refinements;
@@ -849,7 +864,7 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
     stats->max_true_residual = 0.0;
     for (int k = 0; k < n; ++k) {
       rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k], nullptr, btmp1.as<double>(),
-                      btmp2.as<double>(), bpart.as<double>(), bdsum.as<double>(), rn2.data(), &dummy);
+                      btmp2.as<double>(), bpart.as<double>(), bdsum.as<double>(), rn2.data(), &dummy, op);
       if (rc) return rc;
       double worst = 0.0;
       for (int s = 0; s < nrhs; ++s) worst = std::max(worst, std::sqrt(rn2[s] / std::max(bn2[s], 1e-300)));
@@ -867,7 +882,11 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
   k_rational<<<dim3(grid_for(nreal, nrhs), nrhs), RED_THREADS, 0, st>>>(nreal, nrhs, n, c0, bw.as<double>(), b, X,
                                                                        bacc.as<double>()); note_launch();
   BRI_LAUNCH_CHECK("k_rational");
-  if ((rc = dirac_kernel(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) return rc;
+  if (op) {
+    if ((rc = op->apply(bz.as<double2>(), bacc.as<double2>(), nrhs, 0))) return rc;
+  } else if ((rc = dirac_kernel(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) {
+    return rc;
+  }
   cnt.matvecs += 1;
   cnt.matvecs64 += 1;
   k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), (double*)y); note_launch();

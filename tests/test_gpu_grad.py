@@ -8,7 +8,7 @@ import torch
 
 import synthetic_fields as sf
 from oracle import grad as ograd
-from paper_1701_00726_gb300 import PREC_F32, PREC_F64, BriError, Lattice, overlap
+from paper_1701_00726_gb300 import PREC_F32, PREC_F64, Lattice, overlap
 
 pytestmark = pytest.mark.gpu
 
@@ -41,13 +41,24 @@ def test_grad_vs_oracle(am, anti):
     assert relerr(g_u.cpu().numpy(), w_u) < 1e-10
 
 
-def test_grad_rejects_clover():
-    dims = (4, 4, 4, 4)
-    lat = Lattice(dims)
-    lat.build_links(torch.from_numpy(sf.gauge_field(dims, 1)).cuda(), 1.0)
-    x = torch.from_numpy(sf.gaussian_source(dims, 1, 2)).cuda()
-    with pytest.raises(BriError, match="clover"):
-        lat.overlap_grad(x, x.clone(), 4)
+@pytest.mark.parametrize("kernel,c_sw,am,anti", [("bri", 1.0, 0.1, False), ("wil", 1.0, 0.0, True),
+                                                 ("wil", 0.0, 0.2, False)])
+def test_grad_clover_and_wilson_vs_oracle(kernel, c_sw, am, anti):
+    """Clover-term adjoint (Sec. 9 force ingredients) and the Wilson-kernel overlap's adjoint
+    against the oracle gradient on the ragged 6x5x4x3 lattice, within 1e-10."""
+    dims = (6, 5, 4, 3)
+    n = 6
+    u = sf.gauge_field(dims, 94)
+    eta = sf.gaussian_source(dims, 2, 95, normalize=True)
+    psi = sf.gaussian_source(dims, 2, 96, normalize=True)
+    lat = Lattice(dims, antiperiodic_t=anti)
+    lat.build_links(torch.from_numpy(u).cuda(), c_sw)
+    lat.set_kernel(kernel)
+    g_psi, g_u, st = lat.overlap_grad(torch.from_numpy(eta).cuda(), torch.from_numpy(psi).cuda(), n, am=am, tol=1e-13)
+    assert st["converged"]
+    w_psi, w_u = ograd.overlap_grad(u, eta, psi, 1.0, n, 1e-13, am=am, antiperiodic_t=anti, c_sw=c_sw, kernel=kernel)
+    assert relerr(g_psi.cpu().numpy(), w_psi) < 1e-10
+    assert relerr(g_u.cpu().numpy(), w_u) < 1e-10
 
 
 def test_grad_finite_differences_8x4():
