@@ -87,6 +87,13 @@ def parse():
     ap.add_argument("--batch-c4", action="store_true",
                     help="time the batched workload instead: 12 point sources on 16^3x32 plus 8 uneven lattices, "
                          "KL order 12, mixed precision, one concurrent batch vs lattice after lattice")
+    ap.add_argument("--c2", action="store_true",
+                    help="time the FP64 cascaded massive solve on 16^3x32 (KL order 16, cascade order 4, c_SW=1) "
+                         "for the Brillouin and Wilson kernels instead")
+    ap.add_argument("--c2-masses", default="0.1", help="comma-separated am values of --c2")
+    ap.add_argument("--c2-tol", type=float, default=1e-10, help="outer relative residual of --c2")
+    ap.add_argument("--c5-grad", action="store_true",
+                    help="time the mixed-precision backward (overlap_grad, KL order 12) on 32^3x64 instead")
     ap.add_argument("--probe-nrhs", type=int, default=1)
     ap.add_argument("--probe-launches", type=int, default=4)
     return ap.parse_args()
@@ -375,8 +382,76 @@ def batch_c4(args):
                       "batch_applies_per_s": applies / tb, "speedup_vs_sequential": ts / tb}), flush=True)
 
 
+def c2_solve(args):
+    """FP64 massive overlap solves (complete form) with cascaded preconditioning on 16^3x32."""
+    import torch
+
+    import synthetic_fields as sf
+    from paper_1701_00726_gb300 import PREC_F64, Lattice
+    dims = (16, 16, 16, 32)
+    u = sf.gauge_field(dims, GAUGE_SEED, 0.1, 3, device="cuda")
+    b = torch.from_numpy(sf.gaussian_source(dims, 1, GAUGE_SEED + 1000)).cuda()
+    lat = Lattice(dims)
+    lat.build_links(torch.from_numpy(u).cuda(), C_SW)
+    del u
+    rows = []
+    for kernel in ("bri", "wil"):
+        lat.set_kernel(kernel)
+        for am in (float(v) for v in args.c2_masses.split(",")):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = lat.overlap_solve(b, 16, 4, rho=RHO, am=am, complete=True, tol=args.c2_tol, prec=PREC_F64)
+            torch.cuda.synchronize()
+            rows.append({"kernel": kernel, "am": am, "seconds": round(time.perf_counter() - t0, 3),
+                         "outer_iterations": st["iterations"], "inner_iterations": st["refinements"],
+                         "kernel_matvecs": st["matvecs"], "true_residual": st["max_true_residual"],
+                         "converged": st["converged"]})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"workload": "FP64 16^3x32 massive overlap solve, complete form, KL order 16 with cascade "
+                                  f"order 4, stout 3x0.1, c_SW=1, rho=1, outer tol {args.c2_tol:g}, FGMRES outer",
+                      "results": rows}), flush=True)
+
+
+def c5_grad(args):
+    """Mixed-precision backward of L = Re<eta, D_ov psi> on 32^3x64 (KL order 12), next to its forward."""
+    import torch
+
+    import synthetic_fields as sf
+    from paper_1701_00726_gb300 import PREC_F32, Lattice
+    dims = (32, 32, 32, 64)
+    u = sf.gauge_field(dims, 3, device="cuda")
+    eta = torch.from_numpy(sf.gaussian_source(dims, 1, 1003, normalize=True)).cuda()
+    psi = torch.from_numpy(sf.gaussian_source(dims, 1, 2003, normalize=True)).cuda()
+    lat = Lattice(dims)
+    lat.build_links(torch.from_numpy(u).cuda(), 0.0)
+    del u
+    lat.overlap_apply(psi, 12, rho=RHO, tol=TOL, prec=PREC_F32)  # warm-up (autotuner, pool)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, stf = lat.overlap_apply(psi, 12, rho=RHO, tol=TOL, prec=PREC_F32)
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, _, stb = lat.overlap_grad(eta, psi, 12, rho=RHO, tol=TOL, prec=PREC_F32)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    print(json.dumps({"workload": "gradient of Re<eta, D_ov psi> on 32^3x64, KL order 12, mixed precision, tol 1e-10, "
+                                  "c_SW=0, w.r.t. psi and the thin links",
+                      "forward_seconds": round(tf, 3), "backward_seconds": round(tb, 3),
+                      "backward_over_forward": round(tb / tf, 3), "forward_iterations": stf["iterations"],
+                      "backward_iterations": stb["iterations"], "backward_converged": stb["converged"],
+                      "device_GB_in_use_after": round((lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info()), 2)}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.c2:
+        c2_solve(args)
+        return
+    if args.c5_grad:
+        c5_grad(args)
+        return
     if args.batch_c4:
         batch_c4(args)
         return

@@ -148,16 +148,20 @@ int overlap_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kin
                   double rho, double am, double scale, double tol, int prec, bri_stats* st);
 
 /* Batched overlap application over several independent lattices (e.g. gauge
- * fields of uneven volume): the same as calling overlap_apply on each context,
- * but all lattices progress concurrently, each on its context's own stream
- * driven by its own host thread, so that small lattices share the GPU.
- * Solver iterations after the first block are replayed from CUDA graphs
- * captured once per active-system count (disabled with BRI_GRAPHS=0 or while
- * the context is profiling); the stencil launch configuration is autotuned per
- * lattice shape and right-hand-side count on first use (BRI_AUTOTUNE=0
- * disables it).  ctxs: nctx distinct contexts on the current device; ys[i],
- * xs[i]: device complex128 [nrhs[i]][V_i][4][3]; st: NULL or an array of nctx
- * statistics.  Returns the worst per-lattice code. */
+ * fields of uneven volume; the multi-rhs trick of App. C extended across
+ * lattices): the same result as overlap_apply on
+ * each context.  The multi-shift phase of every lattice and right-hand side
+ * runs as one system table: each stencil launch walks a device-side work list
+ * of (lattice, right-hand side, 128-site block) items, the CG scalars and
+ * convergence flags of every system stay in device memory, and the iterations
+ * run inside one CUDA graph whose conditional WHILE node repeats the
+ * iteration until every system has converged (or reached the iteration cap),
+ * with no host polling.  For the mixed precisions the FP64 residuals, FP32
+ * corrections and the final application then run per lattice, concurrently
+ * on the contexts' own streams.  At most 32 contexts, all on the current
+ * device, each with the Brillouin kernel; ys[i], xs[i]: device complex128
+ * [nrhs[i]][V_i][4][3]; st: NULL or an array of nctx statistics.  Returns the
+ * worst per-lattice code. */
 int overlap_apply_batch(bri_ctx* const* ctxs, int nctx, void* const* ys, const void* const* xs, const int* nrhs,
                         int n, int kind, double rho, double am, double scale, double tol, int prec, bri_stats* st);
 

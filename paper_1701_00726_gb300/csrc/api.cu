@@ -389,34 +389,18 @@ int overlap_apply_batch(bri_ctx* const* ctxs, int nctx, void* const* ys, const v
     int rc = check_solver(ctxs[i], ys[i], xs[i], nrhs[i], n, rho, tol, prec, "overlap_apply_batch");
     if (rc) return rc;
   }
-  int dev = 0;
-  cudaGetDevice(&dev);
-  // autotune every lattice's stencil launches first, one lattice at a time
+  if (!std::isfinite(am) || am >= 2.0 * rho) {
+    set_error("overlap_apply_batch: the traditional massive form needs am < 2 rho");
+    return BRI_ERR_INVALID;
+  }
+  // autotune every lattice's stencil launches (used by the per-lattice
+  // refinement) first, one lattice at a time
   for (int i = 0; i < nctx; ++i) {
     int rc = pretune_stencils(ctxs[i], prec);
     if (rc) return rc;
   }
-  std::vector<int> rcs(nctx, BRI_OK);
-  std::vector<std::string> errs(nctx);
-  std::vector<std::thread> pool;
-  pool.reserve(nctx);
-  for (int i = 0; i < nctx; ++i) {
-    pool.emplace_back([&, i]() {
-      cudaSetDevice(dev);
-      rcs[i] = overlap_apply(ctxs[i], ys[i], xs[i], nrhs[i], n, kind, rho, am, scale, tol, prec, st ? &st[i] : nullptr);
-      if (rcs[i] < 0) errs[i] = bri_last_error();
-    });
-  }
-  for (auto& t : pool) t.join();
-  int worst = BRI_OK;
-  for (int i = 0; i < nctx; ++i) {
-    if (rcs[i] < 0) {
-      set_error("overlap_apply_batch: lattice " + std::to_string(i) + ": " + errs[i]);
-      return rcs[i];
-    }
-    worst = std::max(worst, rcs[i]);
-  }
-  return worst;
+  const double k = (1.0 - am / (2.0 * rho)) * rho;
+  return batch_sign_apply(ctxs, nctx, ys, xs, nrhs, n, kind, rho, scale, tol, prec, k, k + am, st);
 }
 
 int bri_profile_enable(bri_ctx* c, int enable) {

@@ -37,16 +37,14 @@ template <int NR> struct BriOcc<double, NR> { static constexpr int v = 2; };
 
 // RG > 1 (with NR = 1): RG consecutive lanes take RG right-hand sides of the
 // same site, so their link loads hit the same addresses and are served once.
-template <typename R, typename LS, int NR, int RG>
-__global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
-    bri_kernel(Geom g, R* __restrict__ y, const R* __restrict__ x, const LS* __restrict__ W,
-               const R* __restrict__ cl, R diag, R sgn, int rhs0, const __grid_constant__ HopTable<R> H) {
-  const int n = blockIdx.x * (blockDim.x / RG) + threadIdx.x / RG;
-  if (n >= g.V) return;
+// The stencil at one site n for NR right-hand sides: xin and yout point at
+// the first right-hand side, the others follow at rstride reals.  Shared by
+// the lattice-wide kernel below and the batched work-list kernel.
+template <typename R, typename LS, int NR>
+__device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ yout, const R* __restrict__ xin,
+                                         int64_t rstride, const LS* __restrict__ W, const R* __restrict__ cl,
+                                         R diag, R sgn, const HopTable<R>& H) {
   const int V = (int)g.V;
-  const int64_t rstride = g.V * 24;
-  const int64_t roff = (int64_t)(rhs0 + (blockIdx.y * RG + threadIdx.x % RG) * NR) * rstride;
-  const R* xin = x + roff;
   int co[4], L[4], str[4];
   {
     int r = n;
@@ -160,8 +158,19 @@ __global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
         acc[r].v[s][aa].im = fma(diag, xc.v[s][aa].im, acc[r].v[s][aa].im);
       }
     if (cl) add_clover(acc[r], xc, cl, g.V, n);
-    store_spinor(y + roff + r * rstride + (int64_t)n * 24, acc[r]);
+    store_spinor(yout + r * rstride + (int64_t)n * 24, acc[r]);
   }
+}
+
+template <typename R, typename LS, int NR, int RG>
+__global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
+    bri_kernel(Geom g, R* __restrict__ y, const R* __restrict__ x, const LS* __restrict__ W,
+               const R* __restrict__ cl, R diag, R sgn, int rhs0, const __grid_constant__ HopTable<R> H) {
+  const int n = blockIdx.x * (blockDim.x / RG) + threadIdx.x / RG;
+  if (n >= g.V) return;
+  const int64_t rstride = g.V * 24;
+  const int64_t roff = (int64_t)(rhs0 + (blockIdx.y * RG + threadIdx.x % RG) * NR) * rstride;
+  bri_site<R, LS, NR>(g, n, y + roff, x + roff, rstride, W, cl, diag, sgn, H);
 }
 
 template <typename R, typename LS, int NR, int RG = 1>

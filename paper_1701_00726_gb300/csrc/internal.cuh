@@ -168,6 +168,11 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
                       int kind, double rho, double am, double scale, double tol, int prec, bri_stats* stats);
 int overlap_solve_impl(bri_ctx* c, double2* x, const double2* b, int n_outer, int n_inner, int kind, double rho,
                        double am, int complete, double tol, int prec, int maxiter, bri_stats* st_out);
+// Batched lattices (overlap_apply_batch): phase 1 on one system table with a
+// work-list stencil and a WHILE-node graph, then per-lattice refinement.
+int batch_sign_apply(bri_ctx* const* cs, int nctx, void* const* ys, const void* const* xs, const int* nrhs, int n,
+                     int kind, double rho, double scale, double tol, int prec, double out_scale, double b_coeff,
+                     bri_stats* stats);
 int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int kind, double rho,
                double scale, double tol, int prec, double out_scale, double b_coeff,
                bri_stats* st, const KernelOp* op = nullptr);

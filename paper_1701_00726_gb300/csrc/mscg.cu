@@ -28,11 +28,15 @@
 // per-system shift, hardest systems first, and converged systems drop out.
 #include "internal.cuh"
 #include "cplx.cuh"
+#include "bri_kernel.cuh"
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <functional>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 namespace bri {
@@ -128,6 +132,9 @@ __global__ void k_shift_dot(int64_t n2, const MsState* __restrict__ st, const ty
 // residual here), then x_i += alpha_i p_i; finally r -= alpha q and the
 // partial ||r||^2.  The base direction p_0 is updated separately (k_update_p0)
 // because the next matrix-vector product needs it.
+// The per-shift coefficients are staged in shared memory once per block (the
+// active shifts compacted to a list), so the element loop reads no scalars
+// from global memory.
 template <typename R>
 __global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__ st,
                                const typename P2<R>::T* __restrict__ q, typename P2<R>::T* r, typename P2<R>::T* p,
@@ -135,22 +142,37 @@ __global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__
   using T = typename P2<R>::T;
   const int s = blockIdx.y;
   if (st[s].done) return;
-  const int nshift = st[s].nshift;
+  __shared__ R sz[NS], sb[NS], sa[NS];
+  __shared__ int sk[NS], snact;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int k = 0; k < st[s].nshift; ++k)
+      if (st[s].active[k]) {
+        sk[m] = k;
+        sz[m] = (R)st[s].zeta[k];
+        sb[m] = (R)st[s].b_s[k];
+        sa[m] = (R)st[s].a_s[k];
+        ++m;
+      }
+    snact = m;
+  }
+  __syncthreads();
+  const int nact = snact;
   const R alpha = (R)st[s].alpha;
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
     T rv = r[s * n2 + i];
-    for (int k = 0; k < nshift; ++k) {
-      if (!st[s].active[k]) continue;
+    for (int m = 0; m < nact; ++m) {
+      const int k = sk[m];
       const int64_t o = ((int64_t)k * nsys + s) * n2 + i;
       T pv = p[o];
       if (k > 0 && !first) {
-        const R z = (R)st[s].zeta[k], bt = (R)st[s].b_s[k];
+        const R z = sz[m], bt = sb[m];
         pv.x = fma(bt, pv.x, z * rv.x);
         pv.y = fma(bt, pv.y, z * rv.y);
         p[o] = pv;
       }
-      const R a = (R)st[s].a_s[k];
+      const R a = sa[m];
       T xv = x[o];
       xv.x = fma(a, pv.x, xv.x);
       xv.y = fma(a, pv.y, xv.y);
@@ -363,6 +385,194 @@ int grid_for(int64_t n, int nsys) {
   int64_t b = (n + RED_THREADS - 1) / RED_THREADS;
   int64_t cap = std::max<int64_t>(1, kMaxPartials / std::max(1, nsys));
   return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// ----------------------------------------------------------------- batched lattices (device work list)
+// Several lattices of uneven volume solved as one system table: system s
+// belongs to lattice sd[s].lat, has n2 complex entries and its vectors sit at
+// complex offset off (r, t, q) and offn + k n2 (shift k of p and x).  The
+// stencil walks a work list of (system, 128-site block) items, so one launch
+// covers every lattice and every right-hand side; items of converged systems
+// return at once.  Per-system scalars are the MsState of the single-lattice
+// solver.
+constexpr int kMaxBatch = 32;
+struct BatchLat {
+  Geom g;
+  const void* W;
+  const void* C;
+  double diag;
+};
+struct BatchTab {
+  int nlat;
+  BatchLat lat[kMaxBatch];
+};
+struct SysDesc {
+  int lat, pad;
+  int64_t n2, off, offn;
+};
+
+template <typename R, typename LS, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+    kb_stencil(const __grid_constant__ BatchTab T, const SysDesc* __restrict__ sd, const int2* __restrict__ items,
+               const MsState* __restrict__ st, typename P2<R>::T* y, const typename P2<R>::T* x, int x_from_p,
+               R sgn, const __grid_constant__ HopTable<R> H) {
+  const int2 it = items[blockIdx.x];
+  const int s = it.x;
+  if (st[s].done) return;
+  const SysDesc d = sd[s];
+  const BatchLat& L = T.lat[d.lat];
+  const int n = it.y * 128 + threadIdx.x;
+  if (n >= L.g.V) return;
+  const R* xin = reinterpret_cast<const R*>(x + (x_from_p ? d.offn : d.off));
+  R* yout = reinterpret_cast<R*>(y + d.off);
+  bri_site<R, LS, 1>(L.g, n, yout, xin, 0, (const LS*)L.W, (const R*)L.C, (R)L.diag, sgn, H);
+}
+
+// r = b, p_k = b, x_k = 0, partial ||b||^2
+template <typename R>
+__global__ void kb_init(const SysDesc* __restrict__ sd, int nshift, const typename P2<R>::T* __restrict__ b,
+                        typename P2<R>::T* r, typename P2<R>::T* p, typename P2<R>::T* x, double* part) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  const SysDesc d = sd[s];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = b[d.off + i];
+    r[d.off + i] = v;
+    for (int k = 0; k < nshift; ++k) {
+      p[d.offn + k * d.n2 + i] = v;
+      x[d.offn + k * d.n2 + i] = T{0, 0};
+    }
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// q += sigma_base p_0 ; partial Re <p_0, q>
+template <typename R>
+__global__ void kb_shift_dot(const SysDesc* __restrict__ sd, const MsState* __restrict__ st,
+                             const typename P2<R>::T* __restrict__ p, typename P2<R>::T* q, double* part) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  if (st[s].done) return;
+  const SysDesc d = sd[s];
+  const R sb = (R)st[s].sig_base;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const T pv = p[d.offn + i];
+    T qv = q[d.off + i];
+    qv.x = fma(sb, pv.x, qv.x);
+    qv.y = fma(sb, pv.y, qv.y);
+    q[d.off + i] = qv;
+    acc += (double)pv.x * qv.x + (double)pv.y * qv.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// the fused shift pass of k_update_fused on the system table
+template <typename R>
+__global__ void kb_update(const SysDesc* __restrict__ sd, const MsState* __restrict__ st,
+                          const typename P2<R>::T* __restrict__ q, typename P2<R>::T* r, typename P2<R>::T* p,
+                          typename P2<R>::T* x, double* part, int first) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  if (st[s].done) return;
+  __shared__ R sz[NS], sb[NS], sa[NS];
+  __shared__ int sk[NS], snact;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int k = 0; k < st[s].nshift; ++k)
+      if (st[s].active[k]) {
+        sk[m] = k;
+        sz[m] = (R)st[s].zeta[k];
+        sb[m] = (R)st[s].b_s[k];
+        sa[m] = (R)st[s].a_s[k];
+        ++m;
+      }
+    snact = m;
+  }
+  __syncthreads();
+  const SysDesc d = sd[s];
+  const int nact = snact;
+  const R alpha = (R)st[s].alpha;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
+    T rv = r[d.off + i];
+    for (int m = 0; m < nact; ++m) {
+      const int k = sk[m];
+      const int64_t o = d.offn + k * d.n2 + i;
+      T pv = p[o];
+      if (k > 0 && !first) {
+        pv.x = fma(sb[m], pv.x, sz[m] * rv.x);
+        pv.y = fma(sb[m], pv.y, sz[m] * rv.y);
+        p[o] = pv;
+      }
+      T xv = x[o];
+      xv.x = fma(sa[m], pv.x, xv.x);
+      xv.y = fma(sa[m], pv.y, xv.y);
+      x[o] = xv;
+    }
+    const T qv = q[d.off + i];
+    rv.x = fma(-alpha, qv.x, rv.x);
+    rv.y = fma(-alpha, qv.y, rv.y);
+    r[d.off + i] = rv;
+    acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// p_0 = r + beta p_0
+template <typename R>
+__global__ void kb_update_p0(const SysDesc* __restrict__ sd, const MsState* __restrict__ st,
+                             const typename P2<R>::T* __restrict__ r, typename P2<R>::T* p) {
+  using T = typename P2<R>::T;
+  const int s = blockIdx.y;
+  if (st[s].done) return;
+  const SysDesc d = sd[s];
+  const R bt = (R)st[s].b_s[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const T rv = r[d.off + i];
+    T pv = p[d.offn + i];
+    pv.x = fma(bt, pv.x, rv.x);
+    pv.y = fma(bt, pv.y, rv.y);
+    p[d.offn + i] = pv;
+  }
+}
+
+// Loop condition of the graph's WHILE node: another iteration while any
+// system is still running (k_scalar_beta marks a system done at its iteration
+// cap, so the loop ends after at most maxiter passes).
+__global__ void kb_while(cudaGraphConditionalHandle h, const MsState* __restrict__ st, int nsys) {
+  int any = 0;
+  for (int s = 0; s < nsys; ++s) any |= !st[s].done;
+  cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+// X_l[k][r][i] (FP64, one lattice's layout) = x[offn(s) + k n2 + i] of system s = s0 + r
+template <typename R>
+__global__ void kb_gather_x(const SysDesc* __restrict__ sd, int s0, int nrhs, int nshift,
+                            const typename P2<R>::T* __restrict__ x, double2* X) {
+  const int r = blockIdx.y, k = blockIdx.z;
+  const SysDesc d = sd[s0 + r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const typename P2<R>::T v = x[d.offn + k * d.n2 + i];
+    X[((int64_t)k * nrhs + r) * d.n2 + i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+// b of one lattice (FP64, [nrhs][n2]) into the system table's vector
+template <typename R>
+__global__ void kb_scatter_b(const SysDesc* __restrict__ sd, int s0, const double2* __restrict__ b,
+                             typename P2<R>::T* out) {
+  const int r = blockIdx.y;
+  const SysDesc d = sd[s0 + r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = b[(int64_t)r * d.n2 + i];
+    out[d.off + i] = typename P2<R>::T{(R)v.x, (R)v.y};
+  }
 }
 
 // ----------------------------------------------------------------- device memory from the stream-ordered pool
@@ -604,6 +814,265 @@ int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X
   return BRI_OK;
 }
 
+// Phases 2 and 3 of the mixed scheme for X = the FP32 multi-shift solution
+// (converted to FP64): one FP64 residual per (shift, rhs), then batched FP32
+// CG corrections of every shift still above tol, with the FP32-tracked
+// residuals checked in FP64 where their rounding error could matter.
+int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig, double m0, double tol, int maxiter,
+                 double* X, double lam_est, SolveInfo& info, const std::function<void(int)>& lap) {
+  cudaStream_t st = c->stream;
+  const int64_t nreal = c->g.V * 24;
+  int rc = BRI_OK;
+  int solve_rc = BRI_OK;
+  Counters& cnt = info.cnt;
+  int& refinements = info.refinements;
+  // phase 2: one FP64 residual per (shift, rhs), r_i = b - (A + sigma_i) X_i
+  DevBuf btmp1, btmp2, bpart, bdsum, bres;
+  if ((rc = btmp1.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  if ((rc = btmp2.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  // The partials buffer serves three grids: the nrhs-wide residuals below,
+  // the correction update (up to 32 systems) and the single-system FP64
+  // verification residuals; grid_for caps every one of them at kMaxPartials.
+  const int nblk_r = grid_for(nreal / 2, nrhs);
+  if ((rc = bpart.alloc(sizeof(double) * std::max<int64_t>((int64_t)nblk_r * nrhs, kMaxPartials), st))) return rc;
+  if ((rc = bdsum.alloc(sizeof(double) * std::max(nrhs, 32), st))) return rc;
+  if ((rc = bres.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
+  std::vector<double> bn2(nrhs), rn2((size_t)n * nrhs), tmp(std::max(nrhs, 32));
+  std::vector<double> err_acc((size_t)n * nrhs, 0.0);  // accumulated FP32 tracking error bound per slot
+  k_residual<<<dim3(nblk_r, nrhs), RED_THREADS, 0, st>>>(nreal, b, b, b, -1.0, nullptr, bpart.as<double>());
+  note_launch();
+  k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
+  BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+  BRI_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < n; ++k) {
+    rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k],
+                    bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(), btmp2.as<double>(),
+                    bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+    if (rc) return rc;
+    for (int s = 0; s < nrhs; ++s) rn2[(size_t)k * nrhs + s] = tmp[s];
+  }
+  btmp1.reset();
+  btmp2.reset();
+  lap(1);
+  // phase 3: FP32 defect correction of every shift still above tol; the
+  // residual is then updated with the FP32 operator applied to the small
+  // correction (its rounding error is ~1e-7 of the old residual).
+  const int max_rounds = 6;
+  for (int round = 0; round < max_rounds; ++round) {
+    std::vector<int> todo;  // slot = k * nrhs + s, hardest (smallest shift) first
+    for (int k = 0; k < n; ++k)
+      for (int sidx = 0; sidx < nrhs; ++sidx) {
+        const size_t slot = (size_t)k * nrhs + sidx;
+        if (std::sqrt(rn2[slot] / std::max(bn2[sidx], 1e-300)) > tol) todo.push_back((int)slot);
+      }
+    if (todo.empty()) break;
+    if (round == max_rounds - 1) {
+      solve_rc = BRI_NOT_CONVERGED;
+      break;
+    }
+    refinements++;
+    const int chunk = 32;
+    for (size_t c0i = 0; c0i < todo.size(); c0i += chunk) {
+      const int m = (int)std::min<size_t>(chunk, todo.size() - c0i);
+      std::vector<double> msig(m), mtol(m);
+      std::vector<long long> slots(m);
+      for (int j = 0; j < m; ++j) {
+        const int slot = todo[c0i + j], k = slot / nrhs, sidx = slot % nrhs;
+        msig[j] = sig[k];
+        slots[j] = slot;
+        const double ratio = tol * std::sqrt(bn2[sidx] / std::max(rn2[slot], 1e-300));
+        mtol[j] = std::min(0.5, std::max(1e-6, 0.3 * ratio));
+      }
+      DevBuf brhs, bsol, bt1, bt2, bslot, bsig;
+      if ((rc = brhs.alloc(sizeof(float) * nreal * m, st))) return rc;
+      if ((rc = bsol.alloc(sizeof(float) * nreal * m, st))) return rc;
+      if ((rc = bslot.alloc(sizeof(long long) * m, st))) return rc;
+      if ((rc = bsig.alloc(sizeof(double) * m, st))) return rc;
+      BRI_CUDA(cudaMemcpyAsync(bslot.as<long long>(), slots.data(), sizeof(long long) * m,
+                               cudaMemcpyHostToDevice, st));
+      BRI_CUDA(cudaMemcpyAsync(bsig.as<double>(), msig.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+      k_gather_f32<<<dim3(512, m), 256, 0, st>>>(nreal, bres.as<double>(), bslot.as<long long>(),
+                                                 brhs.as<float>()); note_launch();
+      int itc = 0;
+      // Corrections always use FP32 links: with BF16 links the operator error
+      // (~4e-3 relative) times the condition number of the small shifts
+      // exceeds one, so a BF16 correction would not reduce the residual.
+      rc = multishift_solve<float>(c, BRI_PREC_F32, m0, m, 1, msig.data(), brhs.as<float>(), bsol.as<float>(),
+                                   1e-5, maxiter, &itc, &cnt, mtol.data());
+      if (rc < 0) return rc;
+      // X += e (FP64); r -= (A + sigma) e with the FP32 operator
+      if ((rc = bt1.alloc(sizeof(float) * nreal * m, st))) return rc;
+      if ((rc = bt2.alloc(sizeof(float) * nreal * m, st))) return rc;
+      // (FP32 links even when the solve used BF16 ones: the update must be
+      // accurate to ~1e-7 of the old residual)
+      if ((rc = dirac_kernel(c, bt1.as<float>(), bsol.as<float>(), m, m0, 0, BRI_PREC_F32, st))) return rc;
+      if ((rc = dirac_kernel(c, bt2.as<float>(), bt1.as<float>(), m, m0, 1, BRI_PREC_F32, st))) return rc;
+      cnt.matvecs += 2;
+      const int nblk_u = grid_for(nreal / 2, m);
+      k_correct<<<dim3(nblk_u, m), RED_THREADS, 0, st>>>(nreal, bslot.as<long long>(), bsig.as<double>(),
+                                                        bsol.as<float>(), bt2.as<float>(), X, bres.as<double>(),
+                                                        bpart.as<double>()); note_launch();
+      k_sum_partials<<<m, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_u, bdsum.as<double>()); note_launch();
+      BRI_LAUNCH_CHECK("refinement update");
+      BRI_CUDA(cudaMemcpyAsync(tmp.data(), bdsum.as<double>(), sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+      BRI_CUDA(cudaStreamSynchronize(st));
+      // The FP32-tracked residual is trusted only where its rounding error,
+      // ~eps32 kappa_i ||r_old|| with kappa_i = (lambda_max + sigma_i)/sigma_i,
+      // is well below tol; otherwise the residual is recomputed in FP64.
+      std::vector<int> verify;
+      for (int j = 0; j < m; ++j) {
+        const int slot = (int)slots[j], k = slot / nrhs, sidx = slot % nrhs;
+        const double kappa = (lam_est + sig[k]) / sig[k];
+        err_acc[slot] += 2e-7 * kappa * std::sqrt(rn2[slot]);
+        const double goal = tol * std::sqrt(bn2[sidx]);
+        rn2[slot] = tmp[j];
+        if (err_acc[slot] > 0.25 * goal && std::sqrt(rn2[slot]) <= goal) verify.push_back(slot);
+      }
+      if (!verify.empty()) {
+        DevBuf v1, v2;
+        if ((rc = v1.alloc(sizeof(double) * nreal, st))) return rc;
+        if ((rc = v2.alloc(sizeof(double) * nreal, st))) return rc;
+        for (int slot : verify) {
+          const int k = slot / nrhs, sidx = slot % nrhs;
+          rc = residual64(c, m0, 1, b + (int64_t)sidx * nreal, X + (int64_t)slot * nreal, sig[k],
+                          bres.as<double>() + (int64_t)slot * nreal, v1.as<double>(), v2.as<double>(),
+                          bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+          if (rc) return rc;
+          rn2[slot] = tmp[0];
+          err_acc[slot] = 0.0;
+        }
+      }
+    }
+  }
+  return solve_rc;
+}
+
+// Phase 1 on the system table: multi-shift CG of every system of every
+// lattice at once.  The first iteration is launched directly; the rest run
+// inside one CUDA graph whose WHILE node repeats the iteration body until
+// every system is done (the condition is set on the device by kb_while), so
+// the host neither polls nor relaunches.  x = [system][shift][n2].
+template <typename R, typename LS>
+int batch_multishift(cudaStream_t st, const BatchTab& tab, const std::vector<SysDesc>& sdh, int nshift,
+                     const double* sig, const typename P2<R>::T* b, typename P2<R>::T* x, double tol, int maxiter,
+                     int* iters_out, Counters* cnt, double* lam_out) {
+  using T = typename P2<R>::T;
+  const int S = (int)sdh.size();
+  int64_t tot = 0, maxn2 = 0;
+  std::vector<int2> items;
+  for (int s = 0; s < S; ++s) {
+    tot += sdh[s].n2;
+    maxn2 = std::max(maxn2, sdh[s].n2);
+    const int64_t nb = (tab.lat[sdh[s].lat].g.V + 127) / 128;
+    for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(s, (int)k));
+  }
+  const int nitems = (int)items.size();
+  const int nblk = grid_for(maxn2, S);
+  DevBuf bsd, bit, br, bt, bq, bp, bst, bpart;
+  int rc;
+  if ((rc = bsd.alloc(sizeof(SysDesc) * S, st))) return rc;
+  if ((rc = bit.alloc(sizeof(int2) * nitems, st))) return rc;
+  if ((rc = br.alloc(sizeof(T) * tot, st))) return rc;
+  if ((rc = bt.alloc(sizeof(T) * tot, st))) return rc;
+  if ((rc = bq.alloc(sizeof(T) * tot, st))) return rc;
+  if ((rc = bp.alloc(sizeof(T) * tot * nshift, st))) return rc;
+  if ((rc = bst.alloc(sizeof(MsState) * S, st))) return rc;
+  if ((rc = bpart.alloc(sizeof(double) * std::max<int64_t>((int64_t)nblk * S, kMaxPartials), st))) return rc;
+  const SysDesc* sd = bsd.as<SysDesc>();
+  MsState* S_ = bst.as<MsState>();
+  double* part = bpart.as<double>();
+  T *r = br.as<T>(), *t = bt.as<T>(), *q = bq.as<T>(), *p = bp.as<T>();
+  std::vector<MsState> hs(S);
+  for (int s = 0; s < S; ++s) {
+    MsState& h = hs[s];
+    memset(&h, 0, sizeof(h));
+    h.nshift = nshift;
+    h.sig_base = sig[0];
+    for (int k = 0; k < nshift; ++k) h.delta[k] = sig[k] - sig[0];
+    h.tol2 = tol * tol;
+    h.maxiter = maxiter;
+  }
+  BRI_CUDA(cudaMemcpyAsync(bsd.p, sdh.data(), sizeof(SysDesc) * S, cudaMemcpyHostToDevice, st));
+  BRI_CUDA(cudaMemcpyAsync(bit.p, items.data(), sizeof(int2) * nitems, cudaMemcpyHostToDevice, st));
+  BRI_CUDA(cudaMemcpyAsync(S_, hs.data(), sizeof(MsState) * S, cudaMemcpyHostToDevice, st));
+  // the host copies above read pageable vectors: complete them before they go out of scope
+  BRI_CUDA(cudaStreamSynchronize(st));
+  const dim3 vg(nblk, S);
+  constexpr int MINB = sizeof(R) == 8 ? 2 : 4;
+  const HopTable<R>& H = hop_table<R>();
+  kb_init<R><<<vg, RED_THREADS, 0, st>>>(sd, nshift, b, r, p, x, part); note_launch();
+  k_scalar_init<<<S, RED_THREADS, 0, st>>>(S_, part, nblk); note_launch();
+  auto iteration = [&](int first) {
+    kb_stencil<R, LS, MINB><<<nitems, 128, 0, st>>>(tab, sd, bit.as<int2>(), S_, t, p, 1, (R)1, H);
+    kb_stencil<R, LS, MINB><<<nitems, 128, 0, st>>>(tab, sd, bit.as<int2>(), S_, q, t, 0, (R)-1, H);
+    kb_shift_dot<R><<<vg, RED_THREADS, 0, st>>>(sd, S_, p, q, part);
+    k_scalar_alpha<<<S, RED_THREADS, 0, st>>>(S_, part, nblk);
+    kb_update<R><<<vg, RED_THREADS, 0, st>>>(sd, S_, q, r, p, x, part, first);
+    k_scalar_beta<<<S, RED_THREADS, 0, st>>>(S_, part, nblk);
+    kb_update_p0<R><<<vg, RED_THREADS, 0, st>>>(sd, S_, r, p);
+  };
+  iteration(1);
+  note_launches(7);
+  BRI_LAUNCH_CHECK("batched multi-shift: first iteration");
+  // graph: WHILE (any system running) { iteration }
+  cudaGraph_t graph = nullptr;
+  BRI_CUDA(cudaGraphCreate(&graph, 0));
+  cudaGraphExec_t gexec = nullptr;
+  auto fail = [&](cudaError_t e, const char* where) {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    cudaGraphDestroy(graph);
+    return cuda_fail(e, where);
+  };
+  cudaGraphConditionalHandle handle;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e, "batched multi-shift: conditional handle");
+  // (the parameter union has no default constructor: zeroed storage instead)
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+  if (e != cudaSuccess) return fail(e, "batched multi-shift: conditional node");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(e, "batched multi-shift: capture");
+  iteration(0);
+  kb_while<<<1, 1, 0, st>>>(handle, S_, S);
+  e = cudaStreamEndCapture(st, &body);
+  if (e != cudaSuccess) return fail(e, "batched multi-shift: end capture");
+  e = cudaGraphInstantiate(&gexec, graph, 0);
+  if (e != cudaSuccess) return fail(e, "batched multi-shift: instantiate");
+  e = cudaGraphLaunch(gexec, st);
+  if (e != cudaSuccess) return fail(e, "batched multi-shift: graph launch");
+  e = cudaMemcpyAsync(hs.data(), S_, sizeof(MsState) * S, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(gexec);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "batched multi-shift: graph run");
+  int maxit = 0, err = 0, notconv = 0;
+  double lm = 0.0;
+  for (int s = 0; s < S; ++s) {
+    maxit = std::max(maxit, hs[s].iters);
+    err |= hs[s].error;
+    if (hs[s].active[0] && !hs[s].error) notconv = 1;
+    lm = std::max(lm, hs[s].lam_max - hs[s].sig_base);
+  }
+  note_launches((long long)8 * std::max(0, maxit - 1));
+  *iters_out = maxit;
+  cnt->matvecs += 2 * maxit;
+  if (sizeof(R) == 8) cnt->matvecs64 += 2 * maxit;
+  if (lam_out) *lam_out = lm;
+  if (err) {
+    set_error("batched multi-shift CG: non-finite or non-positive curvature in a reduction");
+    return BRI_ERR_NONFINITE;
+  }
+  return notconv ? BRI_NOT_CONVERGED : BRI_OK;
+}
+
 }  // namespace
 
 // Solve (A + sigma_k) X_k = b_s for every shift k < n and system s < nsys,
@@ -663,124 +1132,8 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
     bb32.reset();
     bx32.reset();
     lap(0);
-    // phase 2: one FP64 residual per (shift, rhs), r_i = b - (A + sigma_i) X_i
-    DevBuf btmp1, btmp2, bpart, bdsum, bres;
-    if ((rc = btmp1.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-    if ((rc = btmp2.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-    // The partials buffer serves three grids: the nrhs-wide residuals below,
-    // the correction update (up to 32 systems) and the single-system FP64
-    // verification residuals; grid_for caps every one of them at kMaxPartials.
-    const int nblk_r = grid_for(nreal / 2, nrhs);
-    if ((rc = bpart.alloc(sizeof(double) * std::max<int64_t>((int64_t)nblk_r * nrhs, kMaxPartials), st))) return rc;
-    if ((rc = bdsum.alloc(sizeof(double) * std::max(nrhs, 32), st))) return rc;
-    if ((rc = bres.alloc(sizeof(double) * nreal * nrhs * n, st))) return rc;
-    std::vector<double> bn2(nrhs), rn2((size_t)n * nrhs), tmp(std::max(nrhs, 32));
-    std::vector<double> err_acc((size_t)n * nrhs, 0.0);  // accumulated FP32 tracking error bound per slot
-    k_residual<<<dim3(nblk_r, nrhs), RED_THREADS, 0, st>>>(nreal, b, b, b, -1.0, nullptr, bpart.as<double>());
-    note_launch();
-    k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
-    BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
-    BRI_CUDA(cudaStreamSynchronize(st));
-    for (int k = 0; k < n; ++k) {
-      rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k],
-                      bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(), btmp2.as<double>(),
-                      bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
-      if (rc) return rc;
-      for (int s = 0; s < nrhs; ++s) rn2[(size_t)k * nrhs + s] = tmp[s];
-    }
-    btmp1.reset();
-    btmp2.reset();
-    lap(1);
-    // phase 3: FP32 defect correction of every shift still above tol; the
-    // residual is then updated with the FP32 operator applied to the small
-    // correction (its rounding error is ~1e-7 of the old residual).
-    const int max_rounds = 6;
-    for (int round = 0; round < max_rounds; ++round) {
-      std::vector<int> todo;  // slot = k * nrhs + s, hardest (smallest shift) first
-      for (int k = 0; k < n; ++k)
-        for (int sidx = 0; sidx < nrhs; ++sidx) {
-          const size_t slot = (size_t)k * nrhs + sidx;
-          if (std::sqrt(rn2[slot] / std::max(bn2[sidx], 1e-300)) > tol) todo.push_back((int)slot);
-        }
-      if (todo.empty()) break;
-      if (round == max_rounds - 1) {
-        solve_rc = BRI_NOT_CONVERGED;
-        break;
-      }
-      refinements++;
-      const int chunk = 32;
-      for (size_t c0i = 0; c0i < todo.size(); c0i += chunk) {
-        const int m = (int)std::min<size_t>(chunk, todo.size() - c0i);
-        std::vector<double> msig(m), mtol(m);
-        std::vector<long long> slots(m);
-        for (int j = 0; j < m; ++j) {
-          const int slot = todo[c0i + j], k = slot / nrhs, sidx = slot % nrhs;
-          msig[j] = sig[k];
-          slots[j] = slot;
-          const double ratio = tol * std::sqrt(bn2[sidx] / std::max(rn2[slot], 1e-300));
-          mtol[j] = std::min(0.5, std::max(1e-6, 0.3 * ratio));
-        }
-        DevBuf brhs, bsol, bt1, bt2, bslot, bsig;
-        if ((rc = brhs.alloc(sizeof(float) * nreal * m, st))) return rc;
-        if ((rc = bsol.alloc(sizeof(float) * nreal * m, st))) return rc;
-        if ((rc = bslot.alloc(sizeof(long long) * m, st))) return rc;
-        if ((rc = bsig.alloc(sizeof(double) * m, st))) return rc;
-        BRI_CUDA(cudaMemcpyAsync(bslot.as<long long>(), slots.data(), sizeof(long long) * m,
-                                 cudaMemcpyHostToDevice, st));
-        BRI_CUDA(cudaMemcpyAsync(bsig.as<double>(), msig.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-        k_gather_f32<<<dim3(512, m), 256, 0, st>>>(nreal, bres.as<double>(), bslot.as<long long>(),
-                                                   brhs.as<float>()); note_launch();
-        int itc = 0;
-        // Corrections always use FP32 links: with BF16 links the operator error
-        // (~4e-3 relative) times the condition number of the small shifts
-        // exceeds one, so a BF16 correction would not reduce the residual.
-        rc = multishift_solve<float>(c, BRI_PREC_F32, m0, m, 1, msig.data(), brhs.as<float>(), bsol.as<float>(),
-                                     1e-5, maxiter, &itc, &cnt, mtol.data());
-        if (rc < 0) return rc;
-        // X += e (FP64); r -= (A + sigma) e with the FP32 operator
-        if ((rc = bt1.alloc(sizeof(float) * nreal * m, st))) return rc;
-        if ((rc = bt2.alloc(sizeof(float) * nreal * m, st))) return rc;
-        // (FP32 links even when the solve used BF16 ones: the update must be
-        // accurate to ~1e-7 of the old residual)
-        if ((rc = dirac_kernel(c, bt1.as<float>(), bsol.as<float>(), m, m0, 0, BRI_PREC_F32, st))) return rc;
-        if ((rc = dirac_kernel(c, bt2.as<float>(), bt1.as<float>(), m, m0, 1, BRI_PREC_F32, st))) return rc;
-        cnt.matvecs += 2;
-        const int nblk_u = grid_for(nreal / 2, m);
-        k_correct<<<dim3(nblk_u, m), RED_THREADS, 0, st>>>(nreal, bslot.as<long long>(), bsig.as<double>(),
-                                                          bsol.as<float>(), bt2.as<float>(), X, bres.as<double>(),
-                                                          bpart.as<double>()); note_launch();
-        k_sum_partials<<<m, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_u, bdsum.as<double>()); note_launch();
-        BRI_LAUNCH_CHECK("refinement update");
-        BRI_CUDA(cudaMemcpyAsync(tmp.data(), bdsum.as<double>(), sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-        BRI_CUDA(cudaStreamSynchronize(st));
-        // The FP32-tracked residual is trusted only where its rounding error,
-        // ~eps32 kappa_i ||r_old|| with kappa_i = (lambda_max + sigma_i)/sigma_i,
-        // is well below tol; otherwise the residual is recomputed in FP64.
-        std::vector<int> verify;
-        for (int j = 0; j < m; ++j) {
-          const int slot = (int)slots[j], k = slot / nrhs, sidx = slot % nrhs;
-          const double kappa = (lam_est + sig[k]) / sig[k];
-          err_acc[slot] += 2e-7 * kappa * std::sqrt(rn2[slot]);
-          const double goal = tol * std::sqrt(bn2[sidx]);
-          rn2[slot] = tmp[j];
-          if (err_acc[slot] > 0.25 * goal && std::sqrt(rn2[slot]) <= goal) verify.push_back(slot);
-        }
-        if (!verify.empty()) {
-          DevBuf v1, v2;
-          if ((rc = v1.alloc(sizeof(double) * nreal, st))) return rc;
-          if ((rc = v2.alloc(sizeof(double) * nreal, st))) return rc;
-          for (int slot : verify) {
-            const int k = slot / nrhs, sidx = slot % nrhs;
-            rc = residual64(c, m0, 1, b + (int64_t)sidx * nreal, X + (int64_t)slot * nreal, sig[k],
-                            bres.as<double>() + (int64_t)slot * nreal, v1.as<double>(), v2.as<double>(),
-                            bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
-            if (rc) return rc;
-            rn2[slot] = tmp[0];
-            err_acc[slot] = 0.0;
-          }
-        }
-      }
-    }
+    solve_rc = refine_mixed(c, b, nrhs, n, sig, m0, tol, maxiter, X, lam_est, info, lap);
+    if (solve_rc < 0) return solve_rc;
     lap(2);
   } else {
     set_error("sign_apply_multishift: unknown precision");
@@ -788,6 +1141,33 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
   }
 
   return solve_rc;
+}
+
+// y = b_coeff b + out_scale D (c0 b + sum_i w_i X_i) for X = [n][nrhs][V*24] FP64
+int finish_sign(bri_ctx* c, double* y, const double* b, int nrhs, int n, double c0, const double* w, const double* X,
+                double m0, double out_scale, double b_coeff, Counters& cnt, const KernelOp* op) {
+  cudaStream_t st = c->stream;
+  const int64_t nreal = c->g.V * 24;
+  int rc = BRI_OK;
+  // y = b_coeff b + out_scale D (c0 b + sum_i w_i X_i)
+  DevBuf bacc, bz, bw;
+  if ((rc = bacc.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  if ((rc = bz.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
+  if ((rc = bw.alloc(sizeof(double) * NS, st))) return rc;
+  BRI_CUDA(cudaMemcpyAsync(bw.as<double>(), w, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  k_rational<<<dim3(grid_for(nreal, nrhs), nrhs), RED_THREADS, 0, st>>>(nreal, nrhs, n, c0, bw.as<double>(), b, X,
+                                                                       bacc.as<double>()); note_launch();
+  BRI_LAUNCH_CHECK("k_rational");
+  if (op) {
+    if ((rc = op->apply(bz.as<double2>(), bacc.as<double2>(), nrhs, 0))) return rc;
+  } else if ((rc = dirac_kernel(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) {
+    return rc;
+  }
+  cnt.matvecs += 1;
+  cnt.matvecs64 += 1;
+  k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), y); note_launch();
+  BRI_LAUNCH_CHECK("k_axpby");
+  return BRI_OK;
 }
 
 // Runs the enclosed solver work on the context's own non-blocking stream
@@ -873,24 +1253,7 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
     }
   }
 
-  // y = b_coeff b + out_scale D (c0 b + sum_i w_i X_i)
-  DevBuf bacc, bz, bw;
-  if ((rc = bacc.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-  if ((rc = bz.alloc(sizeof(double) * nreal * nrhs, st))) return rc;
-  if ((rc = bw.alloc(sizeof(double) * NS, st))) return rc;
-  BRI_CUDA(cudaMemcpyAsync(bw.as<double>(), w, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  k_rational<<<dim3(grid_for(nreal, nrhs), nrhs), RED_THREADS, 0, st>>>(nreal, nrhs, n, c0, bw.as<double>(), b, X,
-                                                                       bacc.as<double>()); note_launch();
-  BRI_LAUNCH_CHECK("k_rational");
-  if (op) {
-    if ((rc = op->apply(bz.as<double2>(), bacc.as<double2>(), nrhs, 0))) return rc;
-  } else if ((rc = dirac_kernel(c, bz.as<double>(), bacc.as<double>(), nrhs, m0, 0, BRI_PREC_F64, st))) {
-    return rc;
-  }
-  cnt.matvecs += 1;
-  cnt.matvecs64 += 1;
-  k_axpby<<<2048, 256, 0, st>>>(nreal * nrhs, b_coeff, b, out_scale, bz.as<double>(), (double*)y); note_launch();
-  BRI_LAUNCH_CHECK("k_axpby");
+  if ((rc = finish_sign(c, (double*)y, b, nrhs, n, c0, w, X, m0, out_scale, b_coeff, cnt, op))) return rc;
   BRI_CUDA(cudaStreamSynchronize(st));
   tph[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - tmark).count();
   if (stats) {
@@ -903,6 +1266,180 @@ int sign_apply(bri_ctx* c, double2* y, const double2* x, int nrhs, int n, int ki
     for (int ph = 0; ph < 4; ++ph) stats->phase_seconds[ph] = tph[ph];
   }
   return solve_rc;
+}
+
+// Batched sign function / overlap over several lattices (row a8): phase 1 of
+// every lattice and right-hand side in one system table (work-list stencil,
+// device-resident scalars, WHILE-node graph); then, for the mixed scheme, the
+// FP64 residuals and FP32 corrections of each lattice, and the final
+// y = b_coeff b + out_scale D (c0 b + sum_i w_i X_i), the lattices concurrently
+// on their own streams (one host thread each).
+int batch_sign_apply(bri_ctx* const* cs, int nctx, void* const* ys, const void* const* xs, const int* nrhs, int n,
+                     int kind, double rho, double scale, double tol, int prec, double out_scale, double b_coeff,
+                     bri_stats* stats) {
+  if (nctx > kMaxBatch) {
+    set_error("overlap_apply_batch: at most 32 lattices per batch");
+    return BRI_ERR_INVALID;
+  }
+  for (int i = 0; i < nctx; ++i)
+    if (cs[i]->kernel != BRI_KERNEL_BRILLOUIN) {
+      set_error("overlap_apply_batch: the batched work-list stencil is the Brillouin kernel's");
+      return BRI_ERR_INVALID;
+    }
+  auto t0 = std::chrono::steady_clock::now();
+  configure_pool_once();
+  double c0, w[NS], sig[NS];
+  int rc = kl_host(n, kind, scale, &c0, w, sig);
+  if (rc) return rc;
+  const double m0 = -rho;
+  const int maxiter = (stats && stats->maxiter > 0) ? stats->maxiter : 20000;
+  for (int i = 0; i < nctx; ++i) BRI_CUDA(cudaStreamSynchronize(cs[i]->stream));
+  cudaStream_t bs = nullptr;
+  BRI_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  } guard{bs};
+  // system table
+  BatchTab tab;
+  memset(&tab, 0, sizeof(tab));
+  tab.nlat = nctx;
+  std::vector<SysDesc> sd;
+  std::vector<int> first_sys(nctx);
+  int64_t off = 0;
+  for (int i = 0; i < nctx; ++i) {
+    bri_ctx* c = cs[i];
+    tab.lat[i].g = c->g;
+    tab.lat[i].diag = 15.0 / 8.0 + m0;
+    if (prec == BRI_PREC_F64) {
+      tab.lat[i].W = c->W64;
+      tab.lat[i].C = c->have_clover ? (const void*)c->C64 : nullptr;
+    } else {
+      tab.lat[i].W = prec == BRI_PREC_F32_BF16 ? (const void*)c->W16 : (const void*)c->W32;
+      tab.lat[i].C = c->have_clover ? (const void*)c->C32 : nullptr;
+    }
+    first_sys[i] = (int)sd.size();
+    for (int r = 0; r < nrhs[i]; ++r) {
+      SysDesc d;
+      d.lat = i;
+      d.pad = 0;
+      d.n2 = c->g.V * 12;
+      d.off = off;
+      d.offn = off * n;
+      off += d.n2;
+      sd.push_back(d);
+    }
+  }
+  const int S = (int)sd.size();
+  DevBuf bsd;
+  if ((rc = bsd.alloc(sizeof(SysDesc) * S, bs))) return rc;
+  BRI_CUDA(cudaMemcpyAsync(bsd.p, sd.data(), sizeof(SysDesc) * S, cudaMemcpyHostToDevice, bs));
+  std::vector<DevBuf> Xs(nctx);
+  SolveInfo info1;
+  int solve_rc = BRI_OK;
+  double lam_est = 0.0;
+  auto phase1 = [&](auto tag, auto ltag) -> int {
+    using R = decltype(tag);
+    using LS = decltype(ltag);
+    using T = typename P2<R>::T;
+    DevBuf bb, bx;
+    int q;
+    if ((q = bb.alloc(sizeof(T) * off, bs))) return q;
+    if ((q = bx.alloc(sizeof(T) * off * n, bs))) return q;
+    for (int i = 0; i < nctx; ++i) {
+      kb_scatter_b<R><<<dim3(grid_for(cs[i]->g.V * 12, nrhs[i]), nrhs[i]), RED_THREADS, 0, bs>>>(
+          bsd.as<SysDesc>(), first_sys[i], (const double2*)xs[i], bb.as<T>());
+      note_launch();
+    }
+    const double tol1 = sizeof(R) == 8 ? tol : std::max(tol, prec == BRI_PREC_F32 ? 1e-7 : 1e-6);
+    q = batch_multishift<R, LS>(bs, tab, sd, n, sig, bb.as<T>(), bx.as<T>(), tol1, maxiter, &info1.iters, &info1.cnt,
+                                &lam_est);
+    if (q < 0) return q;
+    solve_rc = std::max(solve_rc, q);
+    for (int i = 0; i < nctx; ++i) {
+      const int64_t nreal = cs[i]->g.V * 24;
+      int qq;
+      if ((qq = Xs[i].alloc(sizeof(double) * nreal * nrhs[i] * n, bs))) return qq;
+      kb_gather_x<R><<<dim3(grid_for(cs[i]->g.V * 12, nrhs[i] * n), nrhs[i], n), RED_THREADS, 0, bs>>>(
+          bsd.as<SysDesc>(), first_sys[i], nrhs[i], n, bx.as<T>(), Xs[i].as<double2>());
+      note_launch();
+    }
+    BRI_LAUNCH_CHECK("batched phase 1");
+    BRI_CUDA(cudaStreamSynchronize(bs));
+    return BRI_OK;
+  };
+  if (prec == BRI_PREC_F64) rc = phase1(double(), double2());
+  else if (prec == BRI_PREC_F32) rc = phase1(float(), float2());
+  else rc = phase1(float(), __nv_bfloat162());
+  if (rc < 0) return rc;
+  lam_est = 1.1 * lam_est + 1e-3;
+  const double t_phase1 = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  // per lattice: refinement (mixed) and the final application, concurrently
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> rcs(nctx, BRI_OK);
+  std::vector<std::string> errs(nctx);
+  std::vector<SolveInfo> infos(nctx);
+  std::vector<std::thread> pool;
+  for (int i = 0; i < nctx; ++i) {
+    pool.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      bri_ctx* c = cs[i];
+      StreamScope scope(c);
+      SolveInfo& inf = infos[i];
+      auto tm = std::chrono::steady_clock::now();
+      auto lap = [&](int ph) {
+        cudaStreamSynchronize(c->stream);
+        auto t1 = std::chrono::steady_clock::now();
+        inf.tph[ph] += std::chrono::duration<double>(t1 - tm).count();
+        tm = t1;
+      };
+      int q = BRI_OK;
+      if (prec != BRI_PREC_F64)
+        q = refine_mixed(c, (const double*)xs[i], nrhs[i], n, sig, m0, tol, maxiter, Xs[i].as<double>(), lam_est, inf,
+                         lap);
+      if (q >= 0) {
+        if (prec != BRI_PREC_F64) lap(2);
+        const int q2 = finish_sign(c, (double*)ys[i], (const double*)xs[i], nrhs[i], n, c0, w, Xs[i].as<double>(), m0,
+                                   out_scale, b_coeff, inf.cnt, nullptr);
+        if (q2) q = q2;
+        cudaStreamSynchronize(c->stream);
+        lap(3);
+      }
+      rcs[i] = q;
+      if (q < 0) errs[i] = bri_last_error();
+    });
+  }
+  for (auto& th : pool) th.join();
+  int worst = solve_rc;
+  for (int i = 0; i < nctx; ++i) {
+    if (rcs[i] < 0) {
+      set_error("overlap_apply_batch: lattice " + std::to_string(i) + ": " + errs[i]);
+      return rcs[i];
+    }
+    worst = std::max(worst, rcs[i]);
+  }
+  const double total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int i = 0; i < nctx; ++i) {
+      bri_stats& s = stats[i];
+      const int want = s.want_true_residual, mi = s.maxiter;
+      memset(&s, 0, sizeof(s));
+      s.want_true_residual = want;
+      s.maxiter = mi;
+      s.iterations = info1.iters;
+      s.matvecs = info1.cnt.matvecs + infos[i].cnt.matvecs;
+      s.matvecs_f64 = info1.cnt.matvecs64 + infos[i].cnt.matvecs64;
+      s.refinements = infos[i].refinements;
+      s.n_shifts = n;
+      s.seconds = total;
+      s.phase_seconds[0] = t_phase1;
+      for (int ph = 1; ph < 4; ++ph) s.phase_seconds[ph] = infos[i].tph[ph];
+    }
+  return worst;
 }
 
 }  // namespace bri
