@@ -104,9 +104,76 @@ __device__ __forceinline__ void pair_terms_c2(float2 acc[4], const float2 u[4], 
   acc[3] = fma2(K[7], w[1], acc[3]);
 }
 
-// One thread per site and right-hand side rhs0 + blockIdx.y.
-template <typename LS>
-__global__ void __launch_bounds__(128, 4)
+// One hop pair on the paired pipe: acc += a (P + Q) + c G (P - Q) with
+// P = W_d(n) x(n+d), Q = W_d(n-d)^dagger x(n-d); w = W_d(n), wm = W_d(n-d)
+// already in registers, K the pair constants of this offset.
+__device__ __forceinline__ void c2_pair(float2 (&acc)[4][3], const float* __restrict__ xin, int mp, int mm,
+                                        const C<float> (&w)[3][3], const C<float> (&wm)[3][3],
+                                        const float2* __restrict__ Kp) {
+  const float2 m2 = bc2(-2.f);
+  // P = W_d(n) x(n+d)
+  float2 P[4][3];
+  {
+    SpinorF2 xs;
+    load_spinor_f2(xs, xin + (int64_t)mp * 24);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float2 ix[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) ix[s] = rot(xs.v[s][b]);
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        const float2 wr = bc2(w[aa][b].re), wi = bc2(w[aa][b].im);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          P[s][aa] = b == 0 ? mul2(wr, xs.v[s][b]) : fma2(wr, xs.v[s][b], P[s][aa]);
+          P[s][aa] = fma2(wi, ix[s], P[s][aa]);
+        }
+      }
+    }
+  }
+  // u = P + W_d(n-d)^dagger x(n-d), vn = u - 2P
+  SpinorF2 xs;
+  load_spinor_f2(xs, xin + (int64_t)mm * 24);
+  float2 U[4][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    float2 ix[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) ix[s] = rot(xs.v[s][b]);
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      const float2 wr = bc2(wm[b][aa].re), nwi = bc2(-wm[b][aa].im);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        U[s][aa] = fma2(wr, xs.v[s][b], b == 0 ? P[s][aa] : U[s][aa]);
+        U[s][aa] = fma2(nwi, ix[s], U[s][aa]);
+      }
+    }
+  }
+  float2 K[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) K[i] = Kp[i];
+#pragma unroll
+  for (int aa = 0; aa < 3; ++aa) {
+    float2 u[4], vn[4], col[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      u[s] = U[s][aa];
+      vn[s] = fma2(m2, P[s][aa], U[s][aa]);
+      col[s] = acc[s][aa];
+    }
+    pair_terms_c2(col, u, vn, K);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[s][aa] = col[s];
+  }
+}
+
+// One thread per site and right-hand side rhs0 + blockIdx.y.  PF as for the
+// scalar kernel: 0 loads both links at the start of each hop pair, 1
+// double-buffers W_d(n) one pair ahead, 2 both links.
+template <typename LS, int PF>
+__global__ void __launch_bounds__(128, PF ? 3 : 4)
     bri_kernel_c2(Geom g, float* __restrict__ y, const float* __restrict__ x, const LS* __restrict__ W,
                   const float* __restrict__ cl, float diag, int rhs0, const __grid_constant__ HopTableC2 H) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,77 +202,46 @@ __global__ void __launch_bounds__(128, 4)
   for (int s = 0; s < 4; ++s)
 #pragma unroll
     for (int aa = 0; aa < 3; ++aa) acc[s][aa] = make_float2(0.f, 0.f);
-  const float2 m2 = bc2(-2.f);
-#pragma unroll 1
-  for (int j = 0; j < 40; ++j) {
-    int mp = 0, mm = 0;
+  auto sites = [&](int j, int& mp, int& mm) {
+    mp = 0;
+    mm = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       const int d = H.site_d[j][mu];
       mp += wrap(co[mu] + d, L[mu]) * str[mu];
       mm += wrap(co[mu] - d, L[mu]) * str[mu];
     }
-    // P = W_d(n) x(n+d)
-    float2 P[4][3];
-    {
-      C<float> w[3][3];
+  };
+  if constexpr (PF == 0) {
+#pragma unroll 1
+    for (int j = 0; j < 40; ++j) {
+      int mp, mm;
+      sites(j, mp, mm);
+      C<float> w[3][3], wm[3][3];
       load_stored_link<float, LS>(w, W, j, n, V);
-      SpinorF2 xs;
-      load_spinor_f2(xs, xin + (int64_t)mp * 24);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        float2 ix[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) ix[s] = rot(xs.v[s][b]);
-#pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          const float2 wr = bc2(w[aa][b].re), wi = bc2(w[aa][b].im);
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            P[s][aa] = b == 0 ? mul2(wr, xs.v[s][b]) : fma2(wr, xs.v[s][b], P[s][aa]);
-            P[s][aa] = fma2(wi, ix[s], P[s][aa]);
-          }
-        }
-      }
+      load_stored_link<float, LS>(wm, W, j, mm, V);
+      c2_pair(acc, xin, mp, mm, w, wm, H.k[j]);
     }
-    // u = P + W_d(n-d)^dagger x(n-d), vn = u - 2P
-    {
-      C<float> w[3][3];
-      load_stored_link<float, LS>(w, W, j, mm, V);
-      SpinorF2 xs;
-      load_spinor_f2(xs, xin + (int64_t)mm * 24);
-      float2 U[4][3];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        float2 ix[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) ix[s] = rot(xs.v[s][b]);
-#pragma unroll
-        for (int aa = 0; aa < 3; ++aa) {
-          const float2 wr = bc2(w[b][aa].re), nwi = bc2(-w[b][aa].im);
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            U[s][aa] = fma2(wr, xs.v[s][b], b == 0 ? P[s][aa] : U[s][aa]);
-            U[s][aa] = fma2(nwi, ix[s], U[s][aa]);
-          }
-        }
+  } else {
+    C<float> wA[3][3], wmA[3][3], wB[3][3], wmB[3][3];
+    int mpA, mmA, mpB, mmB;
+    sites(0, mpA, mmA);
+    load_stored_link<float, LS>(wA, W, 0, n, V);
+    if (PF == 2) load_stored_link<float, LS>(wmA, W, 0, mmA, V);
+#pragma unroll 1
+    for (int j = 0; j < 40; j += 2) {
+      sites(j + 1, mpB, mmB);
+      load_stored_link<float, LS>(wB, W, j + 1, n, V);
+      if (PF == 2) load_stored_link<float, LS>(wmB, W, j + 1, mmB, V);
+      if (PF == 1) load_stored_link<float, LS>(wmA, W, j, mmA, V);
+      c2_pair(acc, xin, mpA, mmA, wA, wmA, H.k[j]);
+      if (j + 2 < 40) {
+        sites(j + 2, mpA, mmA);
+        load_stored_link<float, LS>(wA, W, j + 2, n, V);
+        if (PF == 2) load_stored_link<float, LS>(wmA, W, j + 2, mmA, V);
       }
-      float2 K[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) K[i] = H.k[j][i];
-#pragma unroll
-      for (int aa = 0; aa < 3; ++aa) {
-        float2 u[4], vn[4], col[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          u[s] = U[s][aa];
-          vn[s] = fma2(m2, P[s][aa], U[s][aa]);
-          col[s] = acc[s][aa];
-        }
-        pair_terms_c2(col, u, vn, K);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) acc[s][aa] = col[s];
-      }
+      if (PF == 1) load_stored_link<float, LS>(wmB, W, j + 1, mmB, V);
+      c2_pair(acc, xin, mpB, mmB, wB, wmB, H.k[j + 1]);
     }
   }
   Spinor<float> xc, out;
@@ -223,9 +259,11 @@ __global__ void __launch_bounds__(128, 4)
 
 template <typename LS>
 inline void launch_bri_c2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
-                          int dagger, int rhs0, int nrhs, int threads, cudaStream_t s) {
+                          int dagger, int rhs0, int nrhs, int threads, int pf, cudaStream_t s) {
   dim3 grid(blocks_for(g.V, threads), nrhs);
-  bri_kernel_c2<LS><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
+  if (pf == 2) bri_kernel_c2<LS, 2><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
+  else if (pf == 1) bri_kernel_c2<LS, 1><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
+  else bri_kernel_c2<LS, 0><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
   note_launch();
 }
 
