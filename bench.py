@@ -440,6 +440,10 @@ def c5_grad(args):
                       "forward_seconds": round(tf, 3), "backward_seconds": round(tb, 3),
                       "backward_over_forward": round(tb / tf, 3), "forward_iterations": stf["iterations"],
                       "backward_iterations": stb["iterations"], "backward_converged": stb["converged"],
+                      "backward_phase_seconds": {"solves": round(stb["phase_seconds"][0], 3),
+                                                 "dx_and_rationals": round(stb["phase_seconds"][1], 3),
+                                                 "forces": round(stb["phase_seconds"][2], 3),
+                                                 "link_backprop": round(stb["phase_seconds"][3], 3)},
                       "device_GB_in_use_after": round((lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info()), 2)}),
           flush=True)
 

@@ -115,16 +115,17 @@ __device__ __forceinline__ void bri_pair(Spinor<R> (&acc)[NR], const R* __restri
 // RG > 1 (with NR = 1): RG consecutive lanes take RG right-hand sides of the
 // same site, so their link loads hit the same addresses and are served once.
 // The stencil at one site n for NR right-hand sides: xin and yout point at
-// the first right-hand side, the others follow at rstride reals.  Shared by
-// the lattice-wide kernel below and the batched work-list kernel.
+// the first right-hand side, the others follow at xstride (input) and ystride
+// (output) reals.  Shared by the lattice-wide kernel below and the batched
+// work-list kernel.
 // PF = 0 loads both links of a hop pair at its start (one memory latency per
 // pair); PF = 1 double-buffers W_d(n), the link streamed from memory, one
 // pair ahead in registers, and PF = 2 both links, so that their latency hides
 // behind the arithmetic of the current pair (at the cost of registers).
 template <typename R, typename LS, int NR, int PF = 0>
 __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ yout, const R* __restrict__ xin,
-                                         int64_t rstride, const LS* __restrict__ W, const R* __restrict__ cl,
-                                         R diag, R sgn, const HopTable<R>& H) {
+                                         int64_t xstride, int64_t ystride, const LS* __restrict__ W,
+                                         const R* __restrict__ cl, R diag, R sgn, const HopTable<R>& H) {
   const int V = (int)g.V;
   int co[4], L[4], str[4];
   {
@@ -166,7 +167,7 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
       C<R> w[3][3], wm[3][3];
       load_stored_link<R, LS>(w, W, j, n, V);
       load_stored_link<R, LS>(wm, W, j, mm, V);
-      bri_pair<R, NR>(acc, xin, rstride, mp, mm, w, wm, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
+      bri_pair<R, NR>(acc, xin, xstride, mp, mm, w, wm, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
                       sgn * H.cs[j][2], sgn * H.cs[j][3]);
     }
   } else {
@@ -182,7 +183,7 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
       load_stored_link<R, LS>(wB, W, j + 1, n, V);
       if (PF == 2) load_stored_link<R, LS>(wmB, W, j + 1, mmB, V);
       if (PF == 1) load_stored_link<R, LS>(wmA, W, j, mmA, V);
-      bri_pair<R, NR>(acc, xin, rstride, mpA, mmA, wA, wmA, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
+      bri_pair<R, NR>(acc, xin, xstride, mpA, mmA, wA, wmA, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
                       sgn * H.cs[j][2], sgn * H.cs[j][3]);
       if (j + 2 < 40) {
         sites(j + 2, mpA, mmA);
@@ -190,14 +191,14 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
         if (PF == 2) load_stored_link<R, LS>(wmA, W, j + 2, mmA, V);
       }
       if (PF == 1) load_stored_link<R, LS>(wmB, W, j + 1, mmB, V);
-      bri_pair<R, NR>(acc, xin, rstride, mpB, mmB, wB, wmB, H.a[j + 1], sgn * H.cs[j + 1][0], sgn * H.cs[j + 1][1],
+      bri_pair<R, NR>(acc, xin, xstride, mpB, mmB, wB, wmB, H.a[j + 1], sgn * H.cs[j + 1][0], sgn * H.cs[j + 1][1],
                       sgn * H.cs[j + 1][2], sgn * H.cs[j + 1][3]);
     }
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     Spinor<R> xc;
-    load_spinor(xc, xin + r * rstride + (int64_t)n * 24);
+    load_spinor(xc, xin + r * xstride + (int64_t)n * 24);
 #pragma unroll
     for (int s = 0; s < 4; ++s)
 #pragma unroll
@@ -206,7 +207,7 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
         acc[r].v[s][aa].im = fma(diag, xc.v[s][aa].im, acc[r].v[s][aa].im);
       }
     if (cl) add_clover(acc[r], xc, cl, g.V, n);
-    store_spinor(yout + r * rstride + (int64_t)n * 24, acc[r]);
+    store_spinor(yout + r * ystride + (int64_t)n * 24, acc[r]);
   }
 }
 
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(128, BriOcc<R, NR, PF>::v)
   if (n >= g.V) return;
   const int64_t rstride = g.V * 24;
   const int64_t roff = (int64_t)(rhs0 + (blockIdx.y * RG + threadIdx.x % RG) * NR) * rstride;
-  bri_site<R, LS, NR, PF>(g, n, y + roff, x + roff, rstride, W, cl, diag, sgn, H);
+  bri_site<R, LS, NR, PF>(g, n, y + roff, x + roff, rstride, rstride, W, cl, diag, sgn, H);
 }
 
 template <typename R, typename LS, int NR, int RG = 1, int PF = 0>

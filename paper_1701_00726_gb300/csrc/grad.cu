@@ -19,6 +19,8 @@
 // plane, the gradient of its leaf sum (kernels k_clover_force, k_clover_links).
 #include "hops.cuh"
 
+#include <chrono>
+
 namespace bri {
 namespace {
 
@@ -458,11 +460,21 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
     for (int k = 0; k < n; ++k) sig_all[(size_t)s * n + k] = sig[k];
   if ((rc = bX.alloc(sizeof(double) * nreal * nsys * n, st))) return rc;
   SolveInfo info;
+  // phase times (stream-synchronised): solves, D X and rationals, forces, link back-propagation
+  double tph[4] = {0, 0, 0, 0};
+  auto tmark = std::chrono::steady_clock::now();
+  auto lap = [&](int ph) {
+    cudaStreamSynchronize(st);
+    const auto t1 = std::chrono::steady_clock::now();
+    tph[ph] += std::chrono::duration<double>(t1 - tmark).count();
+    tmark = t1;
+  };
   const int maxiter = (stats && stats->maxiter > 0) ? stats->maxiter : 20000;
   rc = solve_shifts(c, bb.as<double>(), nsys, n, sig_all.data(), m0, tol, prec, maxiter, bX.as<double>(), info);
   if (rc < 0) return rc;
   if (rc > solve_rc) solve_rc = rc;
   double* X = bX.as<double>();
+  lap(0);
 
   // y = c0 psi + sum w_i x_i ; D X for every shift and system
   Buf bw;
@@ -482,6 +494,7 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
   if ((rc = dirac_kernel(c, bDX.as<double>(), X, nsys * n, m0, 0, BRI_PREC_F64, st))) return rc;
   BRI_LAUNCH_CHECK("overlap_grad solves");
 
+  lap(1);
   // transporter gradients from all (u, v, weight) pairs
   const bool wilson = c->kernel == BRI_KERNEL_WILSON;
   const HopTable<double>& htab = wilson ? wilson_hop_table() : hop_table<double>();
@@ -535,6 +548,7 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
     BRI_CUDA(cudaStreamSynchronize(st));  // the pair list buffer is reused
   }
 
+  lap(2);
   // back through the path average to the thin links (the Wilson kernel's
   // transporters are the links: one-hop level only)
   Buf bT, bGU;
@@ -567,6 +581,8 @@ int overlap_grad_impl(bri_ctx* c, double* g_psi, double* g_U, const double* eta,
     stats->matvecs_f64 = info.cnt.matvecs64 + 1 + nsys * n;
     stats->refinements = info.refinements;
     stats->n_shifts = n;
+    lap(3);
+    for (int ph = 0; ph < 4; ++ph) stats->phase_seconds[ph] = tph[ph];
   }
   return solve_rc;
 }

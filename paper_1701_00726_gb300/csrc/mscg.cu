@@ -411,21 +411,26 @@ struct SysDesc {
   int64_t n2, off, offn;
 };
 
-template <typename R, typename LS, int MINB>
+// NR = 2: the item's system s and s + 1 (same lattice, adjacent in the table)
+// share the link loads, as in the lattice-wide kernel with two right-hand
+// sides per thread; the pair is skipped only when both have converged.
+template <typename R, typename LS, int NR, int MINB>
 __global__ void __launch_bounds__(128, MINB)
     kb_stencil(const __grid_constant__ BatchTab T, const SysDesc* __restrict__ sd, const int2* __restrict__ items,
                const MsState* __restrict__ st, typename P2<R>::T* y, const typename P2<R>::T* x, int x_from_p,
-               R sgn, const __grid_constant__ HopTable<R> H) {
+               int nshift, R sgn, const __grid_constant__ HopTable<R> H) {
   const int2 it = items[blockIdx.x];
   const int s = it.x;
-  if (st[s].done) return;
+  const bool live = !st[s].done || (NR == 2 && !st[s + 1].done);
+  if (!live) return;
   const SysDesc d = sd[s];
   const BatchLat& L = T.lat[d.lat];
   const int n = it.y * 128 + threadIdx.x;
   if (n >= L.g.V) return;
   const R* xin = reinterpret_cast<const R*>(x + (x_from_p ? d.offn : d.off));
   R* yout = reinterpret_cast<R*>(y + d.off);
-  bri_site<R, LS, 1>(L.g, n, yout, xin, 0, (const LS*)L.W, (const R*)L.C, (R)L.diag, sgn, H);
+  const int64_t xstride = 2 * (x_from_p ? (int64_t)nshift * d.n2 : d.n2), ystride = 2 * d.n2;
+  bri_site<R, LS, NR>(L.g, n, yout, xin, xstride, ystride, (const LS*)L.W, (const R*)L.C, (R)L.diag, sgn, H);
 }
 
 // r = b, p_k = b, x_k = 0, partial ||b||^2
@@ -959,14 +964,20 @@ int batch_multishift(cudaStream_t st, const BatchTab& tab, const std::vector<Sys
   using T = typename P2<R>::T;
   const int S = (int)sdh.size();
   int64_t tot = 0, maxn2 = 0;
-  std::vector<int2> items;
+  // work items: (first system of a same-lattice pair, block) and (single system, block)
+  std::vector<int2> items2, items1;
   for (int s = 0; s < S; ++s) {
     tot += sdh[s].n2;
     maxn2 = std::max(maxn2, sdh[s].n2);
-    const int64_t nb = (tab.lat[sdh[s].lat].g.V + 127) / 128;
-    for (int64_t k = 0; k < nb; ++k) items.push_back(make_int2(s, (int)k));
   }
-  const int nitems = (int)items.size();
+  for (int s = 0; s < S;) {
+    const int64_t nb = (tab.lat[sdh[s].lat].g.V + 127) / 128;
+    const bool pair = s + 1 < S && sdh[s + 1].lat == sdh[s].lat;
+    for (int64_t k = 0; k < nb; ++k) (pair ? items2 : items1).push_back(make_int2(s, (int)k));
+    s += pair ? 2 : 1;
+  }
+  const int n2items = (int)items2.size(), n1items = (int)items1.size();
+  const int nitems = n2items + n1items;
   const int nblk = grid_for(maxn2, S);
   DevBuf bsd, bit, br, bt, bq, bp, bst, bpart;
   int rc;
@@ -993,18 +1004,31 @@ int batch_multishift(cudaStream_t st, const BatchTab& tab, const std::vector<Sys
     h.maxiter = maxiter;
   }
   BRI_CUDA(cudaMemcpyAsync(bsd.p, sdh.data(), sizeof(SysDesc) * S, cudaMemcpyHostToDevice, st));
-  BRI_CUDA(cudaMemcpyAsync(bit.p, items.data(), sizeof(int2) * nitems, cudaMemcpyHostToDevice, st));
+  if (n2items)
+    BRI_CUDA(cudaMemcpyAsync(bit.p, items2.data(), sizeof(int2) * n2items, cudaMemcpyHostToDevice, st));
+  if (n1items)
+    BRI_CUDA(cudaMemcpyAsync(bit.as<int2>() + n2items, items1.data(), sizeof(int2) * n1items, cudaMemcpyHostToDevice,
+                             st));
   BRI_CUDA(cudaMemcpyAsync(S_, hs.data(), sizeof(MsState) * S, cudaMemcpyHostToDevice, st));
   // the host copies above read pageable vectors: complete them before they go out of scope
   BRI_CUDA(cudaStreamSynchronize(st));
   const dim3 vg(nblk, S);
-  constexpr int MINB = sizeof(R) == 8 ? 2 : 4;
+  constexpr int MINB1 = sizeof(R) == 8 ? 2 : 4, MINB2 = sizeof(R) == 8 ? 2 : 3;
   const HopTable<R>& H = hop_table<R>();
+  const int2* it2 = bit.as<int2>();
+  const int2* it1 = bit.as<int2>() + n2items;
+  auto stencil = [&](typename P2<R>::T* out, const typename P2<R>::T* in, int from_p, R sgn) {
+    if (n2items)
+      kb_stencil<R, LS, 2, MINB2><<<n2items, 128, 0, st>>>(tab, sd, it2, S_, out, in, from_p, nshift, sgn, H);
+    if (n1items)
+      kb_stencil<R, LS, 1, MINB1><<<n1items, 128, 0, st>>>(tab, sd, it1, S_, out, in, from_p, nshift, sgn, H);
+  };
+  const int nst = (n2items ? 1 : 0) + (n1items ? 1 : 0);  // stencil launches per application
   kb_init<R><<<vg, RED_THREADS, 0, st>>>(sd, nshift, b, r, p, x, part); note_launch();
   k_scalar_init<<<S, RED_THREADS, 0, st>>>(S_, part, nblk); note_launch();
   auto iteration = [&](int first) {
-    kb_stencil<R, LS, MINB><<<nitems, 128, 0, st>>>(tab, sd, bit.as<int2>(), S_, t, p, 1, (R)1, H);
-    kb_stencil<R, LS, MINB><<<nitems, 128, 0, st>>>(tab, sd, bit.as<int2>(), S_, q, t, 0, (R)-1, H);
+    stencil(t, p, 1, (R)1);
+    stencil(q, t, 0, (R)-1);
     kb_shift_dot<R><<<vg, RED_THREADS, 0, st>>>(sd, S_, p, q, part);
     k_scalar_alpha<<<S, RED_THREADS, 0, st>>>(S_, part, nblk);
     kb_update<R><<<vg, RED_THREADS, 0, st>>>(sd, S_, q, r, p, x, part, first);
@@ -1012,7 +1036,7 @@ int batch_multishift(cudaStream_t st, const BatchTab& tab, const std::vector<Sys
     kb_update_p0<R><<<vg, RED_THREADS, 0, st>>>(sd, S_, r, p);
   };
   iteration(1);
-  note_launches(7);
+  note_launches(5 + 2 * nst);
   BRI_LAUNCH_CHECK("batched multi-shift: first iteration");
   // graph: WHILE (any system running) { iteration }
   cudaGraph_t graph = nullptr;
@@ -1061,7 +1085,7 @@ int batch_multishift(cudaStream_t st, const BatchTab& tab, const std::vector<Sys
     if (hs[s].active[0] && !hs[s].error) notconv = 1;
     lm = std::max(lm, hs[s].lam_max - hs[s].sig_base);
   }
-  note_launches((long long)8 * std::max(0, maxit - 1));
+  note_launches((long long)(6 + 2 * nst) * std::max(0, maxit - 1));
   *iters_out = maxit;
   cnt->matvecs += 2 * maxit;
   if (sizeof(R) == 8) cnt->matvecs64 += 2 * maxit;

@@ -24,8 +24,10 @@ def relerr(got, want):
 
 
 def _inputs(i, dims):
+    """Lattice 0: the 12 point sources (six two-rhs work items); lattice 1: three sources (one
+    two-rhs item and a single); the others one source each (single items)."""
     u = sf.gauge_field(dims, 20 + i, 0.1, 3)
-    src = sf.point_sources(dims) if i == 0 else sf.gaussian_source(dims, 1, 40 + i)
+    src = sf.point_sources(dims) if i == 0 else sf.gaussian_source(dims, 3 if i == 1 else 1, 40 + i)
     return u, src
 
 
