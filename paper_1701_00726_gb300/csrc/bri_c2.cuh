@@ -169,11 +169,9 @@ __device__ __forceinline__ void c2_pair(float2 (&acc)[4][3], const float* __rest
   }
 }
 
-// One thread per site and right-hand side rhs0 + blockIdx.y.  PF as for the
-// scalar kernel: 0 loads both links at the start of each hop pair, 1
-// double-buffers W_d(n) one pair ahead, 2 both links.
-template <typename LS, int PF>
-__global__ void __launch_bounds__(128, PF ? 3 : 4)
+// One thread per site and right-hand side rhs0 + blockIdx.y.
+template <typename LS>
+__global__ void __launch_bounds__(128, 4)
     bri_kernel_c2(Geom g, float* __restrict__ y, const float* __restrict__ x, const LS* __restrict__ W,
                   const float* __restrict__ cl, float diag, int rhs0, const __grid_constant__ HopTableC2 H) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,37 +210,14 @@ __global__ void __launch_bounds__(128, PF ? 3 : 4)
       mm += wrap(co[mu] - d, L[mu]) * str[mu];
     }
   };
-  if constexpr (PF == 0) {
 #pragma unroll 1
-    for (int j = 0; j < 40; ++j) {
-      int mp, mm;
-      sites(j, mp, mm);
-      C<float> w[3][3], wm[3][3];
-      load_stored_link<float, LS>(w, W, j, n, V);
-      load_stored_link<float, LS>(wm, W, j, mm, V);
-      c2_pair(acc, xin, mp, mm, w, wm, H.k[j]);
-    }
-  } else {
-    C<float> wA[3][3], wmA[3][3], wB[3][3], wmB[3][3];
-    int mpA, mmA, mpB, mmB;
-    sites(0, mpA, mmA);
-    load_stored_link<float, LS>(wA, W, 0, n, V);
-    if (PF == 2) load_stored_link<float, LS>(wmA, W, 0, mmA, V);
-#pragma unroll 1
-    for (int j = 0; j < 40; j += 2) {
-      sites(j + 1, mpB, mmB);
-      load_stored_link<float, LS>(wB, W, j + 1, n, V);
-      if (PF == 2) load_stored_link<float, LS>(wmB, W, j + 1, mmB, V);
-      if (PF == 1) load_stored_link<float, LS>(wmA, W, j, mmA, V);
-      c2_pair(acc, xin, mpA, mmA, wA, wmA, H.k[j]);
-      if (j + 2 < 40) {
-        sites(j + 2, mpA, mmA);
-        load_stored_link<float, LS>(wA, W, j + 2, n, V);
-        if (PF == 2) load_stored_link<float, LS>(wmA, W, j + 2, mmA, V);
-      }
-      if (PF == 1) load_stored_link<float, LS>(wmB, W, j + 1, mmB, V);
-      c2_pair(acc, xin, mpB, mmB, wB, wmB, H.k[j + 1]);
-    }
+  for (int j = 0; j < 40; ++j) {
+    int mp, mm;
+    sites(j, mp, mm);
+    C<float> w[3][3], wm[3][3];
+    load_stored_link<float, LS>(w, W, j, n, V);
+    load_stored_link<float, LS>(wm, W, j, mm, V);
+    c2_pair(acc, xin, mp, mm, w, wm, H.k[j]);
   }
   Spinor<float> xc, out;
   load_spinor(xc, xin + (int64_t)n * 24);
@@ -259,11 +234,9 @@ __global__ void __launch_bounds__(128, PF ? 3 : 4)
 
 template <typename LS>
 inline void launch_bri_c2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
-                          int dagger, int rhs0, int nrhs, int threads, int pf, cudaStream_t s) {
+                          int dagger, int rhs0, int nrhs, int threads, cudaStream_t s) {
   dim3 grid(blocks_for(g.V, threads), nrhs);
-  if (pf == 2) bri_kernel_c2<LS, 2><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
-  else if (pf == 1) bri_kernel_c2<LS, 1><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
-  else bri_kernel_c2<LS, 0><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
+  bri_kernel_c2<LS><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
   note_launch();
 }
 

@@ -33,11 +33,9 @@
 namespace bri {
 
 // Resident blocks of 128 threads per SM the kernels are compiled for (the
-// register budget): the prefetching variants hold a second set of links.
-template <typename R, int NR, int PF> struct BriOcc {
-  static constexpr int v = NR == 1 ? (PF ? 3 : 4) : (PF ? 2 : 3);
-};
-template <int NR, int PF> struct BriOcc<double, NR, PF> { static constexpr int v = 2; };
+// register budget).
+template <typename R, int NR> struct BriOcc { static constexpr int v = NR == 1 ? 4 : 3; };
+template <int NR> struct BriOcc<double, NR> { static constexpr int v = 2; };
 
 // One hop pair (stored offset d and its opposite) for NR right-hand sides:
 // acc += a (P + Q) + c G (P - Q) with P = W_d(n) x(n+d), Q = W_d(n-d)^dagger x(n-d),
@@ -118,11 +116,7 @@ __device__ __forceinline__ void bri_pair(Spinor<R> (&acc)[NR], const R* __restri
 // the first right-hand side, the others follow at xstride (input) and ystride
 // (output) reals.  Shared by the lattice-wide kernel below and the batched
 // work-list kernel.
-// PF = 0 loads both links of a hop pair at its start (one memory latency per
-// pair); PF = 1 double-buffers W_d(n), the link streamed from memory, one
-// pair ahead in registers, and PF = 2 both links, so that their latency hides
-// behind the arithmetic of the current pair (at the cost of registers).
-template <typename R, typename LS, int NR, int PF = 0>
+template <typename R, typename LS, int NR>
 __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ yout, const R* __restrict__ xin,
                                          int64_t xstride, int64_t ystride, const LS* __restrict__ W,
                                          const R* __restrict__ cl, R diag, R sgn, const HopTable<R>& H) {
@@ -158,42 +152,17 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
   // The pair of opposite hops shares a, c and G = sum_mu s_mu gamma_mu:
   //   W x+ M_d + W'^dagger M_{-d} x- = a (P + Q) + c G (P - Q),
   //   P = W_d(n) x(n+d),  Q = W_d(n-d)^dagger x(n-d)   (M_{+-d} = a +- c G).
-  if constexpr (PF == 0) {
-    // both links and both source spinors are loaded before any arithmetic
+  // both links and both source spinors are loaded before any arithmetic, so
+  // one memory latency is exposed per pair of hops
 #pragma unroll 1
-    for (int j = 0; j < 40; ++j) {
-      int mp, mm;
-      sites(j, mp, mm);
-      C<R> w[3][3], wm[3][3];
-      load_stored_link<R, LS>(w, W, j, n, V);
-      load_stored_link<R, LS>(wm, W, j, mm, V);
-      bri_pair<R, NR>(acc, xin, xstride, mp, mm, w, wm, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
-                      sgn * H.cs[j][2], sgn * H.cs[j][3]);
-    }
-  } else {
-    C<R> wA[3][3], wmA[3][3], wB[3][3], wmB[3][3];
-    int mpA, mmA, mpB, mmB;
-    sites(0, mpA, mmA);
-    load_stored_link<R, LS>(wA, W, 0, n, V);
-    if (PF == 2) load_stored_link<R, LS>(wmA, W, 0, mmA, V);
-#pragma unroll 1
-    for (int j = 0; j < 40; j += 2) {
-      // loads of pair j + 1 go out before the arithmetic of pair j
-      sites(j + 1, mpB, mmB);
-      load_stored_link<R, LS>(wB, W, j + 1, n, V);
-      if (PF == 2) load_stored_link<R, LS>(wmB, W, j + 1, mmB, V);
-      if (PF == 1) load_stored_link<R, LS>(wmA, W, j, mmA, V);
-      bri_pair<R, NR>(acc, xin, xstride, mpA, mmA, wA, wmA, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
-                      sgn * H.cs[j][2], sgn * H.cs[j][3]);
-      if (j + 2 < 40) {
-        sites(j + 2, mpA, mmA);
-        load_stored_link<R, LS>(wA, W, j + 2, n, V);
-        if (PF == 2) load_stored_link<R, LS>(wmA, W, j + 2, mmA, V);
-      }
-      if (PF == 1) load_stored_link<R, LS>(wmB, W, j + 1, mmB, V);
-      bri_pair<R, NR>(acc, xin, xstride, mpB, mmB, wB, wmB, H.a[j + 1], sgn * H.cs[j + 1][0], sgn * H.cs[j + 1][1],
-                      sgn * H.cs[j + 1][2], sgn * H.cs[j + 1][3]);
-    }
+  for (int j = 0; j < 40; ++j) {
+    int mp, mm;
+    sites(j, mp, mm);
+    C<R> w[3][3], wm[3][3];
+    load_stored_link<R, LS>(w, W, j, n, V);
+    load_stored_link<R, LS>(wm, W, j, mm, V);
+    bri_pair<R, NR>(acc, xin, xstride, mp, mm, w, wm, H.a[j], sgn * H.cs[j][0], sgn * H.cs[j][1],
+                    sgn * H.cs[j][2], sgn * H.cs[j][3]);
   }
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
@@ -211,22 +180,22 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
   }
 }
 
-template <typename R, typename LS, int NR, int RG, int PF>
-__global__ void __launch_bounds__(128, BriOcc<R, NR, PF>::v)
+template <typename R, typename LS, int NR, int RG>
+__global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
     bri_kernel(Geom g, R* __restrict__ y, const R* __restrict__ x, const LS* __restrict__ W,
                const R* __restrict__ cl, R diag, R sgn, int rhs0, const __grid_constant__ HopTable<R> H) {
   const int n = blockIdx.x * (blockDim.x / RG) + threadIdx.x / RG;
   if (n >= g.V) return;
   const int64_t rstride = g.V * 24;
   const int64_t roff = (int64_t)(rhs0 + (blockIdx.y * RG + threadIdx.x % RG) * NR) * rstride;
-  bri_site<R, LS, NR, PF>(g, n, y + roff, x + roff, rstride, rstride, W, cl, diag, sgn, H);
+  bri_site<R, LS, NR>(g, n, y + roff, x + roff, rstride, rstride, W, cl, diag, sgn, H);
 }
 
-template <typename R, typename LS, int NR, int RG = 1, int PF = 0>
+template <typename R, typename LS, int NR, int RG = 1>
 inline void launch_bri_nr(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, R sgn, int rhs0,
                           int groups, int threads, cudaStream_t s) {
   dim3 grid(blocks_for(g.V, threads / RG), groups);
-  bri_kernel<R, LS, NR, RG, PF><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0, hop_table<R>());
+  bri_kernel<R, LS, NR, RG><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0, hop_table<R>());
   note_launch();
 }
 
@@ -242,17 +211,11 @@ inline void launch_with(const StencilConfig& cf, const Geom& g, R* y, const R* x
       launch_bri_nr<R, LS, 1, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
       done = (nrhs / 2) * 2;
     } else if (cf.pairs == 2) {
-      launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs, cf.threads, cf.pf, s);
+      launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs, cf.threads, s);
       done = nrhs;
     } else if (nrhs >= 2 && cf.pairs) {
-      if (cf.pf) launch_bri_nr<R, LS, 2, 1, 1>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
-      else launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
+      launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
       done = (nrhs / 2) * 2;
-    }
-    if (nrhs > done && cf.pf) {
-      if (cf.pf == 2) launch_bri_nr<R, LS, 1, 1, 2>(g, y, x, W, cl, diag, sgn, done, nrhs - done, cf.threads, s);
-      else launch_bri_nr<R, LS, 1, 1, 1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, cf.threads, s);
-      done = nrhs;
     }
   }
   if (nrhs > done) launch_bri_nr<R, LS, 1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, cf.threads, s);
@@ -266,12 +229,10 @@ template <typename R, typename LS>
 StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, R sgn, int nrhs,
                            cudaStream_t s) {
   StencilConfig def;
-  if (const char* f = getenv("BRI_STENCIL_FORCE")) {  // "pairs,threads,rg[,pf]", read on every launch
+  if (const char* f = getenv("BRI_STENCIL_FORCE")) {  // "pairs,threads,rg", read on every launch
     StencilConfig cf;
-    const int got = sscanf(f, "%d,%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg, &cf.pf);
-    if (got < 4) cf.pf = 0;
-    if (got >= 3 && cf.pairs >= 0 && cf.pairs <= 2 && (cf.threads == 64 || cf.threads == 128) &&
-        (cf.rg == 1 || cf.rg == 2 || cf.rg == 4) && cf.pf >= 0 && cf.pf <= 2)
+    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && cf.pairs >= 0 && cf.pairs <= 2 &&
+        (cf.threads == 64 || cf.threads == 128) && (cf.rg == 1 || cf.rg == 2 || cf.rg == 4))
       return cf;
   }
   if (!autotune_enabled()) {
@@ -300,29 +261,26 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
     for (int th : {64, 128}) cands.push_back(StencilConfig{2, th, 1});
   if (sizeof(R) == 4 && nrhs >= 2) cands.push_back(StencilConfig{0, 128, 2});
   if (sizeof(R) == 4 && nrhs >= 4) cands.push_back(StencilConfig{0, 128, 4});
-  if (sizeof(R) == 4) {  // links double-buffered one hop pair ahead
-    cands.push_back(StencilConfig{0, 128, 1, 1});
-    cands.push_back(StencilConfig{0, 128, 1, 2});
-    cands.push_back(StencilConfig{2, 128, 1, 1});
-    cands.push_back(StencilConfig{2, 128, 1, 2});
-    if (nrhs >= 2) cands.push_back(StencilConfig{1, 128, 1, 1});
-  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
   StencilConfig bestc = def;
+  // every rhs-count class is timed on its representative count (1, 2 or 4
+  // right-hand sides of the caller's buffers), so tuning a launch with many
+  // right-hand sides costs no more than one with four
+  const int nt = std::min(nrhs, cls);
   for (const StencilConfig& cf : cands) {
-    launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s);  // warm
+    launch_with(cf, g, y, x, W, cl, diag, sgn, nt, s);  // warm
     cudaEventRecord(e0, s);
-    for (int rep = 0; rep < 3; ++rep) launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s);
+    for (int rep = 0; rep < 3; ++rep) launch_with(cf, g, y, x, W, cl, diag, sgn, nt, s);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (getenv("BRI_TUNE_LOG"))
-      fprintf(stderr, "bri autotune %s: pairs=%d threads=%d rg=%d pf=%d  %.4f ms\n", key, cf.pairs, cf.threads, cf.rg,
-              cf.pf, ms / 3);
+      fprintf(stderr, "bri autotune %s: pairs=%d threads=%d rg=%d  %.4f ms\n", key, cf.pairs, cf.threads, cf.rg,
+              ms / 3);
     if (ms < best) {
       best = ms;
       bestc = cf;

@@ -138,7 +138,6 @@ struct StencilConfig {
   int pairs = 1;
   int threads = 128;
   int rg = 1;  // right-hand sides on consecutive lanes (shared link loads), instead of pairs
-  int pf = 0;  // FP32 links double-buffered one hop pair ahead: 1 = W_d(n), 2 = both links
 };
 bool tune_lookup(const char* key, StencilConfig* out);
 void tune_store(const char* key, const StencilConfig& cf);
