@@ -169,16 +169,19 @@ __device__ __forceinline__ void c2_pair(float2 (&acc)[4][3], const float* __rest
   }
 }
 
-// One thread per site and right-hand side rhs0 + blockIdx.y.
+// One thread per site and right-hand side; the grid order of rhs and site
+// blocks is that of stencil_grid (gfirst).
 template <typename LS>
 __global__ void __launch_bounds__(128, 4)
     bri_kernel_c2(Geom g, float* __restrict__ y, const float* __restrict__ x, const LS* __restrict__ W,
-                  const float* __restrict__ cl, float diag, int rhs0, const __grid_constant__ HopTableC2 H) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+                  const float* __restrict__ cl, float diag, int rhs0, int gfirst,
+                  const __grid_constant__ HopTableC2 H) {
+  const int grp = gfirst ? blockIdx.x : blockIdx.y, blk = gfirst ? blockIdx.y : blockIdx.x;
+  const int n = blk * blockDim.x + threadIdx.x;
   if (n >= g.V) return;
   const int V = (int)g.V;
   const int64_t rstride = g.V * 24;
-  const int64_t roff = (int64_t)(rhs0 + blockIdx.y) * rstride;
+  const int64_t roff = (int64_t)(rhs0 + grp) * rstride;
   const float* xin = x + roff;
   int co[4], L[4], str[4];
   {
@@ -235,8 +238,8 @@ __global__ void __launch_bounds__(128, 4)
 template <typename LS>
 inline void launch_bri_c2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
                           int dagger, int rhs0, int nrhs, int threads, cudaStream_t s) {
-  dim3 grid(blocks_for(g.V, threads), nrhs);
-  bri_kernel_c2<LS><<<grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, hop_table_c2(dagger));
+  const StencilGrid sg = stencil_grid(blocks_for(g.V, threads), nrhs);
+  bri_kernel_c2<LS><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, sg.gfirst, hop_table_c2(dagger));
   note_launch();
 }
 

@@ -133,7 +133,9 @@ int pair_rhs_enabled();
 int autotune_enabled();
 // Launch configuration of the FP32 stencil: pairs = 0 one right-hand side per
 // thread, 1 two per thread (shared link loads), 2 the paired-FP32 kernel
-// (bri_c2.cuh, one per thread); and the block size.
+// (bri_c2.cuh, one per thread), 3 / 4 the staged-link kernel (bri_tma.cuh) with
+// one / two right-hand sides per thread (FP32 paired links only; 160 threads);
+// and the block size.
 struct StencilConfig {
   int pairs = 1;
   int threads = 128;
@@ -142,6 +144,19 @@ struct StencilConfig {
 bool tune_lookup(const char* key, StencilConfig* out);
 void tune_store(const char* key, const StencilConfig& cf);
 std::mutex& tune_mutex();
+
+// Grid of a stencil launch: the right-hand-side groups in x (fastest, so the
+// groups of one site block run together and reuse its links from L2) and the
+// site blocks in y, unless there are more site blocks than a grid's y extent
+// allows; gfirst tells the kernel which order was chosen.
+struct StencilGrid {
+  dim3 grid;
+  int gfirst;
+};
+inline StencilGrid stencil_grid(int64_t site_blocks, int groups) {
+  if (site_blocks <= 65535) return StencilGrid{dim3((unsigned)groups, (unsigned)site_blocks), 1};
+  return StencilGrid{dim3((unsigned)site_blocks, (unsigned)groups), 0};
+}
 
 // Host-side launchers (one translation unit per precision).
 template <typename R, typename LS>
