@@ -177,7 +177,7 @@ def stencil_traffic_per_launch(traffic, vol, nlaunch, units, prec):
 def stencil_source_hash():
     """Hash of the FP32 stencil's sources (kernel header and shared helpers)."""
     h = hashlib.sha256()
-    for f in ("bri_kernel.cuh", "bri_c2.cuh", "bri_tma.cuh", "hops.cuh", "stencil.cuh", "cplx.cuh"):
+    for f in ("bri_kernel.cuh", "bri_c2.cuh", "hops.cuh", "stencil.cuh", "cplx.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1701_00726_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -541,8 +541,7 @@ def main():
     t_alu = alg_flops / (fp32_peak * 1e12)
     traffic = stencil_traffic()
     lt = "bf16x2" if prec == PREC_F32_BF16 else "float2"
-    common = {"kernel": f"bri_kernel<float,{lt},1|2> | bri_kernel_c2<{lt}> | bri_kernel_staged<1|2> "
-                        "(autotuned per rhs count)",
+    common = {"kernel": f"bri_kernel<float,{lt},1|2> | bri_kernel_c2<{lt}> (autotuned per rhs count)",
               "launches": nlaunch, "avg_launch_ms": round(kms / max(nlaunch, 1), 4),
               "avg_rhs_per_launch": round(units / max(nlaunch, 1) / vol, 3),
               "alg_bytes_per_launch": int(alg_bytes / max(nlaunch, 1)),

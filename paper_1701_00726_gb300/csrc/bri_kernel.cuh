@@ -180,12 +180,6 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
   }
 }
 
-}  // namespace bri
-
-#include "bri_tma.cuh"
-
-namespace bri {
-
 template <typename R, typename LS, int NR, int RG>
 __global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
     bri_kernel(Geom g, R* __restrict__ y, const R* __restrict__ x, const LS* __restrict__ W,
@@ -206,32 +200,12 @@ inline void launch_bri_nr(const Geom& g, R* y, const R* x, const LS* W, const R*
   note_launch();
 }
 
-template <int NR>
-inline void launch_bri_staged(const Geom& g, float* y, const float* x, const float2* W, const float* cl, float diag,
-                              float sgn, int rhs0, int groups, cudaStream_t s) {
-  const StencilGrid sg = stencil_grid(blocks_for(g.V, kStageSites), groups);
-  bri_kernel_staged<NR><<<sg.grid, 160, kStagedSmem, s>>>(g, y, x, W, cl, diag, sgn, rhs0, sg.gfirst,
-                                                          hop_table<float>());
-  note_launch();
-}
-
 template <typename R, typename LS>
 inline void launch_with(const StencilConfig& cf, const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag,
                         R sgn, int nrhs, cudaStream_t s) {
   int done = 0;
-  if constexpr (sizeof(R) == 4 && sizeof(LS) == 8) {  // FP32 paired links: the staged-link kernel
-    if (cf.pairs == 4 && nrhs >= 2) {
-      launch_bri_staged<2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, s);
-      done = (nrhs / 2) * 2;
-    }
-    if (cf.pairs >= 3 && nrhs > done) {
-      launch_bri_staged<1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, s);
-      done = nrhs;
-    }
-  }
   if constexpr (sizeof(R) == 4) {
-    if (done == nrhs) {
-    } else if (cf.rg == 4 && nrhs >= 4) {
+    if (cf.rg == 4 && nrhs >= 4) {
       launch_bri_nr<R, LS, 1, 4>(g, y, x, W, cl, diag, sgn, 0, nrhs / 4, cf.threads, s);
       done = (nrhs / 4) * 4;
     } else if (cf.rg == 2 && nrhs >= 2) {
@@ -258,7 +232,7 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
   StencilConfig def;
   if (const char* f = getenv("BRI_STENCIL_FORCE")) {  // "pairs,threads,rg", read on every launch
     StencilConfig cf;
-    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && cf.pairs >= 0 && cf.pairs <= 4 &&
+    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && cf.pairs >= 0 && cf.pairs <= 2 &&
         (cf.threads == 64 || cf.threads == 128) && (cf.rg == 1 || cf.rg == 2 || cf.rg == 4))
       return cf;
   }
@@ -288,10 +262,6 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
     for (int th : {64, 128}) cands.push_back(StencilConfig{2, th, 1});
   if (sizeof(R) == 4 && nrhs >= 2) cands.push_back(StencilConfig{0, 128, 2});
   if (sizeof(R) == 4 && nrhs >= 4) cands.push_back(StencilConfig{0, 128, 4});
-  if (sizeof(R) == 4 && sizeof(LS) == 8) {  // staged links (FP32 paired layout)
-    cands.push_back(StencilConfig{3, 128, 1});
-    if (nrhs >= 2) cands.push_back(StencilConfig{4, 128, 1});
-  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -133,9 +133,7 @@ int pair_rhs_enabled();
 int autotune_enabled();
 // Launch configuration of the FP32 stencil: pairs = 0 one right-hand side per
 // thread, 1 two per thread (shared link loads), 2 the paired-FP32 kernel
-// (bri_c2.cuh, one per thread), 3 / 4 the staged-link kernel (bri_tma.cuh) with
-// one / two right-hand sides per thread (FP32 paired links only; 160 threads);
-// and the block size.
+// (bri_c2.cuh, one per thread); and the block size.
 struct StencilConfig {
   int pairs = 1;
   int threads = 128;
