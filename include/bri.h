@@ -205,7 +205,8 @@ int overlap_grad(bri_ctx* ctx, void* g_psi, void* g_U, const void* eta, const vo
  *
  * All solver workspace comes from one 32 MiB static device array that every
  * device loading the library holds until exit.  Limit: V * nrhs * (2n + 3) *
- * 192 bytes plus 64 KB + 4 KB * nrhs of state must fit in it (e.g. 8^4 with
+ * 192 bytes plus 64 KB + 4 KB * nrhs + 8 B * nrhs * ceil(V / 64) + 512 B of
+ * state and reduction partials must fit in it (e.g. 8^4 with
  * nrhs = 1 and n <= 19, or 4^4 with nrhs <= 16 at n = 16); larger problems
  * are rejected with BRI_ERR_INVALID and a message.  The array's device address
  * is looked up (cudaGetSymbolAddress) by bri_build_links on the device that is

@@ -56,6 +56,21 @@ inline const HopTableC2& hop_table_c2(int dagger) {
 }
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+// Sum of v over the block (FP64, fixed order), valid in thread 0.
+__device__ __forceinline__ double block_total_c2(double v) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 swp(float2 v) { return make_float2(v.y, v.x); }
@@ -171,14 +186,17 @@ __device__ __forceinline__ void c2_pair(float2 (&acc)[4][3], const float* __rest
 
 // One thread per site and right-hand side; the grid order of rhs and site
 // blocks is that of stencil_grid (gfirst).
-template <typename LS>
+template <typename LS, bool EPI>
 __global__ void __launch_bounds__(128, 4)
     bri_kernel_c2(Geom g, float* __restrict__ y, const float* __restrict__ x, const LS* __restrict__ W,
                   const float* __restrict__ cl, float diag, int rhs0, int gfirst,
-                  const __grid_constant__ HopTableC2 H) {
+                  const __grid_constant__ HopTableC2 H, ShiftDot<float> sd) {
   const int grp = gfirst ? blockIdx.x : blockIdx.y, blk = gfirst ? blockIdx.y : blockIdx.x;
-  const int n = blk * blockDim.x + threadIdx.x;
-  if (n >= g.V) return;
+  const int n0 = blk * blockDim.x + threadIdx.x;
+  if (!EPI && n0 >= g.V) return;
+  // with the epilogue every thread takes part in the block's reduction
+  const bool valid = n0 < g.V;
+  const int n = valid ? n0 : 0;
   const int V = (int)g.V;
   const int64_t rstride = g.V * 24;
   const int64_t roff = (int64_t)(rhs0 + grp) * rstride;
@@ -232,14 +250,40 @@ __global__ void __launch_bounds__(128, 4)
       out.v[s][aa].im = fmaf(diag, xc.v[s][aa].im, acc[s][aa].y);
     }
   if (cl) add_clover(out, xc, cl, g.V, n);
-  store_spinor(y + roff + (int64_t)n * 24, out);
+  if constexpr (EPI) {
+    const int s = rhs0 + grp;
+    const float sg = (float)sd.sig[s];
+    Spinor<float> pv;
+    load_spinor(pv, sd.p + roff + (int64_t)n * 24);
+    float dt = 0.f;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        out.v[sp][aa].re = fmaf(sg, pv.v[sp][aa].re, out.v[sp][aa].re);
+        out.v[sp][aa].im = fmaf(sg, pv.v[sp][aa].im, out.v[sp][aa].im);
+        dt = fmaf(pv.v[sp][aa].re, out.v[sp][aa].re, dt);
+        dt = fmaf(pv.v[sp][aa].im, out.v[sp][aa].im, dt);
+      }
+    if (valid) store_spinor(y + roff + (int64_t)n * 24, out);
+    const double t = block_total_c2(valid ? (double)dt : 0.0);
+    if (threadIdx.x == 0) sd.part[(int64_t)s * (gfirst ? gridDim.y : gridDim.x) + blk] = t;
+  } else {
+    store_spinor(y + roff + (int64_t)n * 24, out);
+  }
 }
 
 template <typename LS>
 inline void launch_bri_c2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
-                          int dagger, int rhs0, int nrhs, int threads, cudaStream_t s) {
+                          int dagger, int rhs0, int nrhs, int threads, cudaStream_t s,
+                          const ShiftDot<float>* sd = nullptr) {
   const StencilGrid sg = stencil_grid(blocks_for(g.V, threads), nrhs);
-  bri_kernel_c2<LS><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, sg.gfirst, hop_table_c2(dagger));
+  if (sd)
+    bri_kernel_c2<LS, true><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, sg.gfirst, hop_table_c2(dagger),
+                                                        *sd);
+  else
+    bri_kernel_c2<LS, false><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, sg.gfirst, hop_table_c2(dagger),
+                                                         ShiftDot<float>{nullptr, nullptr, nullptr});
   note_launch();
 }
 

@@ -3,7 +3,8 @@
 
 namespace bri {
 template int launch_bri_t<float, float2>(const Geom&, float*, const float*, const float2*, const float*, float, int,
-                                         int, cudaStream_t);
+                                         int, cudaStream_t, const ShiftDot<float>*, int*);
 template int launch_bri_t<float, __nv_bfloat162>(const Geom&, float*, const float*, const __nv_bfloat162*,
-                                                 const float*, float, int, int, cudaStream_t);
+                                                 const float*, float, int, int, cudaStream_t, const ShiftDot<float>*,
+                                                 int*);
 }  // namespace bri

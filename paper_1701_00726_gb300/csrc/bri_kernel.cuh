@@ -116,10 +116,14 @@ __device__ __forceinline__ void bri_pair(Spinor<R> (&acc)[NR], const R* __restri
 // the first right-hand side, the others follow at xstride (input) and ystride
 // (output) reals.  Shared by the lattice-wide kernel below and the batched
 // work-list kernel.
+// With pin set (the fused solver epilogue) the output becomes q = D x + psig[r]
+// pin at this site and dots[r] = Re<pin, q> over its 12 complex components.
 template <typename R, typename LS, int NR>
 __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ yout, const R* __restrict__ xin,
                                          int64_t xstride, int64_t ystride, const LS* __restrict__ W,
-                                         const R* __restrict__ cl, R diag, R sgn, const HopTable<R>& H) {
+                                         const R* __restrict__ cl, R diag, R sgn, const HopTable<R>& H,
+                                         const R* __restrict__ pin = nullptr, const R* psig = nullptr,
+                                         R* dots = nullptr) {
   const int V = (int)g.V;
   int co[4], L[4], str[4];
   {
@@ -176,50 +180,113 @@ __device__ __forceinline__ void bri_site(const Geom& g, int n, R* __restrict__ y
         acc[r].v[s][aa].im = fma(diag, xc.v[s][aa].im, acc[r].v[s][aa].im);
       }
     if (cl) add_clover(acc[r], xc, cl, g.V, n);
+    if (pin) {
+      Spinor<R> pv;
+      load_spinor(pv, pin + r * ystride + (int64_t)n * 24);
+      R dt = 0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          acc[r].v[s][aa].re = fma(psig[r], pv.v[s][aa].re, acc[r].v[s][aa].re);
+          acc[r].v[s][aa].im = fma(psig[r], pv.v[s][aa].im, acc[r].v[s][aa].im);
+          dt = fma(pv.v[s][aa].re, acc[r].v[s][aa].re, dt);
+          dt = fma(pv.v[s][aa].im, acc[r].v[s][aa].im, dt);
+        }
+      dots[r] = dt;
+    }
     store_spinor(yout + r * ystride + (int64_t)n * 24, acc[r]);
   }
 }
 
-template <typename R, typename LS, int NR, int RG>
+// Sum of v over the block (FP64, fixed order), valid in thread 0.
+__device__ __forceinline__ double block_total(double v) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
+
+template <typename R, typename LS, int NR, int RG, bool EPI>
 __global__ void __launch_bounds__(128, BriOcc<R, NR>::v)
     bri_kernel(Geom g, R* __restrict__ y, const R* __restrict__ x, const LS* __restrict__ W,
-               const R* __restrict__ cl, R diag, R sgn, int rhs0, int gfirst, const __grid_constant__ HopTable<R> H) {
+               const R* __restrict__ cl, R diag, R sgn, int rhs0, int gfirst, const __grid_constant__ HopTable<R> H,
+               ShiftDot<R> sd) {
   const int grp = gfirst ? blockIdx.x : blockIdx.y, blk = gfirst ? blockIdx.y : blockIdx.x;
   const int n = blk * (blockDim.x / RG) + threadIdx.x / RG;
-  if (n >= g.V) return;
   const int64_t rstride = g.V * 24;
-  const int64_t roff = (int64_t)(rhs0 + (grp * RG + threadIdx.x % RG) * NR) * rstride;
-  bri_site<R, LS, NR>(g, n, y + roff, x + roff, rstride, rstride, W, cl, diag, sgn, H);
+  const int s0 = rhs0 + (grp * RG + threadIdx.x % RG) * NR;  // first right-hand side of this thread
+  const int64_t roff = (int64_t)s0 * rstride;
+  if constexpr (!EPI) {
+    if (n >= g.V) return;
+    bri_site<R, LS, NR>(g, n, y + roff, x + roff, rstride, rstride, W, cl, diag, sgn, H);
+  } else {  // RG == 1: every thread of the block has the same right-hand sides
+    R dots[NR], sig[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      dots[r] = 0;
+      sig[r] = (R)sd.sig[s0 + r];
+    }
+    if (n < g.V)
+      bri_site<R, LS, NR>(g, n, y + roff, x + roff, rstride, rstride, W, cl, diag, sgn, H, sd.p + roff, sig, dots);
+    const int nb = gfirst ? gridDim.y : gridDim.x;  // site blocks
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const double t = block_total((double)dots[r]);
+      if (threadIdx.x == 0) sd.part[(int64_t)(s0 + r) * nb + blk] = t;
+    }
+  }
 }
 
 template <typename R, typename LS, int NR, int RG = 1>
 inline void launch_bri_nr(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, R sgn, int rhs0,
-                          int groups, int threads, cudaStream_t s) {
+                          int groups, int threads, cudaStream_t s, const ShiftDot<R>* sd = nullptr) {
   const StencilGrid sg = stencil_grid(blocks_for(g.V, threads / RG), groups);
-  bri_kernel<R, LS, NR, RG><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0, sg.gfirst, hop_table<R>());
+  if constexpr (RG == 1) {
+    if (sd) {
+      bri_kernel<R, LS, NR, 1, true><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0, sg.gfirst,
+                                                                 hop_table<R>(), *sd);
+      note_launch();
+      return;
+    }
+  }
+  bri_kernel<R, LS, NR, RG, false><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, sgn, rhs0, sg.gfirst,
+                                                              hop_table<R>(), ShiftDot<R>{nullptr, nullptr, nullptr});
   note_launch();
 }
 
+// sd (optional): the fused solver epilogue; its partials are indexed by the
+// site blocks of the chosen block size (blocks_for(V, threads)).
 template <typename R, typename LS>
 inline void launch_with(const StencilConfig& cf, const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag,
-                        R sgn, int nrhs, cudaStream_t s) {
+                        R sgn, int nrhs, cudaStream_t s, const ShiftDot<R>* sd = nullptr) {
   int done = 0;
   if constexpr (sizeof(R) == 4) {
-    if (cf.rg == 4 && nrhs >= 4) {
+    if (sd && cf.rg > 1) {  // rhs on consecutive lanes has no fused form: two rhs per thread instead
+      if (nrhs >= 2) launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s, sd);
+      done = (nrhs / 2) * 2;
+    } else if (cf.rg == 4 && nrhs >= 4) {
       launch_bri_nr<R, LS, 1, 4>(g, y, x, W, cl, diag, sgn, 0, nrhs / 4, cf.threads, s);
       done = (nrhs / 4) * 4;
     } else if (cf.rg == 2 && nrhs >= 2) {
       launch_bri_nr<R, LS, 1, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
       done = (nrhs / 2) * 2;
     } else if (cf.pairs == 2) {
-      launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs, cf.threads, s);
+      launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs, cf.threads, s, sd);
       done = nrhs;
     } else if (nrhs >= 2 && cf.pairs) {
-      launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s);
+      launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s, sd);
       done = (nrhs / 2) * 2;
     }
   }
-  if (nrhs > done) launch_bri_nr<R, LS, 1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, cf.threads, s);
+  if (nrhs > done) launch_bri_nr<R, LS, 1>(g, y, x, W, cl, diag, sgn, done, nrhs - done, cf.threads, s, sd);
 }
 
 // Autotuner: on the first launch for a (device, lattice, rhs-count class,
@@ -296,10 +363,11 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
 
 template <typename R, typename LS>
 int launch_bri_t(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, int nrhs, int dagger,
-                 cudaStream_t s) {
+                 cudaStream_t s, const ShiftDot<R>* sd, int* sd_blocks) {
   const R sgn = (R)(dagger ? -1 : 1);
   const StencilConfig cf = tuned_config(g, y, x, W, cl, diag, sgn, nrhs, s);
-  launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s);
+  if (sd_blocks) *sd_blocks = (int)blocks_for(g.V, cf.threads);
+  launch_with(cf, g, y, x, W, cl, diag, sgn, nrhs, s, sd);
   BRI_LAUNCH_CHECK("bri_kernel");
   return BRI_OK;
 }

@@ -34,6 +34,43 @@ void tune_store(const char* key, const StencilConfig& cf) {
   g_tune[key] = cf;
 }
 
+// D^dagger x + sigma_s p with the per-block partials of Re<p_s, .> (the fused
+// solver epilogue, Brillouin kernel): sd_blocks receives the number of
+// partials per system.
+int dirac_bri_shiftdot(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int prec, cudaStream_t s,
+                       const void* p, const double* sig, double* part, int* sd_blocks) {
+  const double diag = 15.0 / 8.0 + m0;
+  cudaEvent_t ev;
+  int rc = prof_begin(c, s, &ev);
+  if (rc) return rc;
+  switch (prec) {
+    case BRI_PREC_F64: {
+      const ShiftDot<double> sd{(const double*)p, sig, part};
+      rc = launch_bri_t<double, double2>(c->g, (double*)y, (const double*)x, c->W64,
+                                       c->have_clover ? c->C64 : nullptr, diag, nrhs, 1, s, &sd, sd_blocks);
+      break;
+    }
+    case BRI_PREC_F32: {
+      const ShiftDot<float> sd{(const float*)p, sig, part};
+      rc = launch_bri_t<float, float2>(c->g, (float*)y, (const float*)x, c->W32,
+                                     c->have_clover ? c->C32 : nullptr, (float)diag, nrhs, 1, s, &sd, sd_blocks);
+      break;
+    }
+    case BRI_PREC_F32_BF16: {
+      const ShiftDot<float> sd{(const float*)p, sig, part};
+      rc = launch_bri_t<float, __nv_bfloat162>(c->g, (float*)y, (const float*)x, c->W16,
+                                             c->have_clover ? c->C32 : nullptr, (float)diag, nrhs, 1, s, &sd,
+                                             sd_blocks);
+      break;
+    }
+    default:
+      set_error("bri_apply: unknown precision");
+      return BRI_ERR_INVALID;
+  }
+  if (rc) return rc;
+  return prof_end(c, s, ev, 0, prec, (double)c->g.V * nrhs);
+}
+
 int dirac_kernel(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec, cudaStream_t s) {
   if (c->kernel == BRI_KERNEL_WILSON) return dirac_wil(c, y, x, nrhs, m0, dagger, prec, s);
   return dirac_bri(c, y, x, nrhs, m0, dagger, prec, s);

@@ -116,6 +116,11 @@ int dirac_bri(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagge
               cudaStream_t s);
 int dirac_wil(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
               cudaStream_t s);
+// The solver's fused D^dagger application: y = D^dagger x + sigma_s p_s and the
+// per-site-block partials of Re<p_s, y> (Brillouin kernel only); sd_blocks
+// receives the number of partials per system (part: [nrhs][sd_blocks]).
+int dirac_bri_shiftdot(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int prec, cudaStream_t s,
+                       const void* p, const double* sig, double* part, int* sd_blocks);
 // The overlap's kernel operator selected on the context (bri_set_kernel):
 // the Brillouin stencil (Eq. def_bril) or the Wilson stencil (Eq. def_wils).
 int dirac_kernel(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,

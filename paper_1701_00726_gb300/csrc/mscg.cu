@@ -86,9 +86,9 @@ __device__ __forceinline__ double block_sum(double v) {
 // Vectors are flat arrays of n2 pairs (re, im) per system; system s at s*n2.
 
 // r = b, p_i = b (all shifts), x_i = 0, partial ||b||^2
-template <typename R>
+template <typename R, typename XT = typename P2<R>::T>
 __global__ void k_init(int64_t n2, int nsys, int nshift, const typename P2<R>::T* __restrict__ b,
-                       typename P2<R>::T* r, typename P2<R>::T* p, typename P2<R>::T* x, double* part) {
+                       typename P2<R>::T* r, typename P2<R>::T* p, XT* x, double* part) {
   using T = typename P2<R>::T;
   const int s = blockIdx.y;
   double acc = 0.0;
@@ -97,7 +97,7 @@ __global__ void k_init(int64_t n2, int nsys, int nshift, const typename P2<R>::T
     r[s * n2 + i] = v;
     for (int k = 0; k < nshift; ++k) {
       p[((int64_t)k * nsys + s) * n2 + i] = v;
-      x[((int64_t)k * nsys + s) * n2 + i] = T{0, 0};
+      x[((int64_t)k * nsys + s) * n2 + i] = XT{0, 0};
     }
     acc += (double)v.x * v.x + (double)v.y * v.y;
   }
@@ -135,14 +135,16 @@ __global__ void k_shift_dot(int64_t n2, const MsState* __restrict__ st, const ty
 // The per-shift coefficients are staged in shared memory once per block (the
 // active shifts compacted to a list), so the element loop reads no scalars
 // from global memory.
-template <typename R>
+template <typename R, typename XT = typename P2<R>::T>
 __global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__ st,
                                const typename P2<R>::T* __restrict__ q, typename P2<R>::T* r, typename P2<R>::T* p,
-                               typename P2<R>::T* x, double* part, int first) {
+                               XT* x, double* part, int first) {
   using T = typename P2<R>::T;
+  using XR = decltype(XT::x);
   const int s = blockIdx.y;
   if (st[s].done) return;
-  __shared__ R sz[NS], sb[NS], sa[NS];
+  __shared__ R sz[NS], sb[NS];
+  __shared__ XR sa[NS];
   __shared__ int sk[NS], snact;
   if (threadIdx.x == 0) {
     int m = 0;
@@ -151,7 +153,7 @@ __global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__
         sk[m] = k;
         sz[m] = (R)st[s].zeta[k];
         sb[m] = (R)st[s].b_s[k];
-        sa[m] = (R)st[s].a_s[k];
+        sa[m] = (XR)st[s].a_s[k];
         ++m;
       }
     snact = m;
@@ -172,10 +174,10 @@ __global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__
         pv.y = fma(bt, pv.y, z * rv.y);
         p[o] = pv;
       }
-      const R a = sa[m];
-      T xv = x[o];
-      xv.x = fma(a, pv.x, xv.x);
-      xv.y = fma(a, pv.y, xv.y);
+      const XR a = sa[m];
+      XT xv = x[o];
+      xv.x = fma(a, (XR)pv.x, xv.x);
+      xv.y = fma(a, (XR)pv.y, xv.y);
       x[o] = xv;
     }
     const T qv = q[s * n2 + i];
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(128, MINB)
 // r = b, p_k = b, x_k = 0, partial ||b||^2
 template <typename R>
 __global__ void kb_init(const SysDesc* __restrict__ sd, int nshift, const typename P2<R>::T* __restrict__ b,
-                        typename P2<R>::T* r, typename P2<R>::T* p, typename P2<R>::T* x, double* part) {
+                        typename P2<R>::T* r, typename P2<R>::T* p, double2* x, double* part) {
   using T = typename P2<R>::T;
   const int s = blockIdx.y;
   const SysDesc d = sd[s];
@@ -446,7 +448,7 @@ __global__ void kb_init(const SysDesc* __restrict__ sd, int nshift, const typena
     r[d.off + i] = v;
     for (int k = 0; k < nshift; ++k) {
       p[d.offn + k * d.n2 + i] = v;
-      x[d.offn + k * d.n2 + i] = T{0, 0};
+      x[d.offn + k * d.n2 + i] = make_double2(0.0, 0.0);
     }
     acc += (double)v.x * v.x + (double)v.y * v.y;
   }
@@ -476,15 +478,16 @@ __global__ void kb_shift_dot(const SysDesc* __restrict__ sd, const MsState* __re
   if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
 }
 
-// the fused shift pass of k_update_fused on the system table
+// the fused shift pass of k_update_fused on the system table (solutions in FP64)
 template <typename R>
 __global__ void kb_update(const SysDesc* __restrict__ sd, const MsState* __restrict__ st,
                           const typename P2<R>::T* __restrict__ q, typename P2<R>::T* r, typename P2<R>::T* p,
-                          typename P2<R>::T* x, double* part, int first) {
+                          double2* x, double* part, int first) {
   using T = typename P2<R>::T;
   const int s = blockIdx.y;
   if (st[s].done) return;
-  __shared__ R sz[NS], sb[NS], sa[NS];
+  __shared__ R sz[NS], sb[NS];
+  __shared__ double sa[NS];
   __shared__ int sk[NS], snact;
   if (threadIdx.x == 0) {
     int m = 0;
@@ -493,7 +496,7 @@ __global__ void kb_update(const SysDesc* __restrict__ sd, const MsState* __restr
         sk[m] = k;
         sz[m] = (R)st[s].zeta[k];
         sb[m] = (R)st[s].b_s[k];
-        sa[m] = (R)st[s].a_s[k];
+        sa[m] = st[s].a_s[k];
         ++m;
       }
     snact = m;
@@ -514,9 +517,9 @@ __global__ void kb_update(const SysDesc* __restrict__ sd, const MsState* __restr
         pv.y = fma(sb[m], pv.y, sz[m] * rv.y);
         p[o] = pv;
       }
-      T xv = x[o];
-      xv.x = fma(sa[m], pv.x, xv.x);
-      xv.y = fma(sa[m], pv.y, xv.y);
+      double2 xv = x[o];
+      xv.x = fma(sa[m], (double)pv.x, xv.x);
+      xv.y = fma(sa[m], (double)pv.y, xv.y);
       x[o] = xv;
     }
     const T qv = q[d.off + i];
@@ -556,16 +559,13 @@ __global__ void kb_while(cudaGraphConditionalHandle h, const MsState* __restrict
   cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
-// X_l[k][r][i] (FP64, one lattice's layout) = x[offn(s) + k n2 + i] of system s = s0 + r
-template <typename R>
+// X_l[k][r][i] (one lattice's layout) = x[offn(s) + k n2 + i] of system s = s0 + r
 __global__ void kb_gather_x(const SysDesc* __restrict__ sd, int s0, int nrhs, int nshift,
-                            const typename P2<R>::T* __restrict__ x, double2* X) {
+                            const double2* __restrict__ x, double2* X) {
   const int r = blockIdx.y, k = blockIdx.z;
   const SysDesc d = sd[s0 + r];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x) {
-    const typename P2<R>::T v = x[d.offn + k * d.n2 + i];
-    X[((int64_t)k * nrhs + r) * d.n2 + i] = make_double2((double)v.x, (double)v.y);
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n2; i += (int64_t)gridDim.x * blockDim.x)
+    X[((int64_t)k * nrhs + r) * d.n2 + i] = x[d.offn + k * d.n2 + i];
 }
 
 // b of one lattice (FP64, [nrhs][n2]) into the system table's vector
@@ -654,11 +654,12 @@ template <> int op_prec<float>(int prec) { return prec == BRI_PREC_F32_BF16 ? BR
 
 
 // Solve (A + sig[s][k]) x[k][s] = b[s] for nsys systems with nshift shifts each.
-// sig: host [nsys][nshift], increasing within a system.
+// sig: host [nsys][nshift], increasing within a system.  x64 (R = float only):
+// the solutions are accumulated in FP64 there instead of in x (x unused).
 template <typename R>
 int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, const double* sig, const R* b, R* x,
                      double tol, int maxiter, int* iters_out, Counters* cnt, const double* tols,
-                     double* lam_out = nullptr, const KernelOp* op = nullptr) {
+                     double* lam_out = nullptr, const KernelOp* op = nullptr, double* x64 = nullptr) {
   using T = typename P2<R>::T;
   cudaStream_t st = c->stream;
   const int64_t n2 = c->g.V * 12;  // complex pairs per system
@@ -691,8 +692,24 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
     h.maxiter = maxiter;
   }
   BRI_CUDA(cudaMemcpyAsync(S, hs.data(), sizeof(MsState) * nsys, cudaMemcpyHostToDevice, st));
+  // Fused D^dagger application (Brillouin kernel): q = D^dagger t + sigma_base p_0
+  // and the partials of Re<p_0, q> come out of the stencil's epilogue, so
+  // k_shift_dot's pass over q and p_0 is not needed.
+  const bool fused = op == nullptr && c->kernel == BRI_KERNEL_BRILLOUIN;
+  DevBuf bsig, bpart_sd;
+  std::vector<double> hsig(nsys);
+  for (int s = 0; s < nsys; ++s) hsig[s] = hs[s].sig_base;
+  if (fused) {
+    if ((rc = bsig.alloc(sizeof(double) * nsys, st))) return rc;
+    if ((rc = bpart_sd.alloc(sizeof(double) * nsys * (size_t)blocks_for(c->g.V, 64), st))) return rc;
+    BRI_CUDA(cudaMemcpyAsync(bsig.p, hsig.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
+  }
   dim3 vg(nblk, nsys);
-  k_init<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, nshift, (const T*)b, r, p, (T*)x, part); note_launch();
+  if (x64)
+    k_init<R, double2><<<vg, RED_THREADS, 0, st>>>(n2, nsys, nshift, (const T*)b, r, p, (double2*)x64, part);
+  else
+    k_init<R><<<vg, RED_THREADS, 0, st>>>(n2, nsys, nshift, (const T*)b, r, p, (T*)x, part);
+  note_launch();
   k_scalar_init<<<nsys, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
   BRI_LAUNCH_CHECK("multishift init");
 
@@ -714,13 +731,25 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
       if (op) {  // an FP64 operator given by the caller (R = double)
         if ((q = op->apply((double2*)t, (const double2*)p, na, 0))) return q;
         if ((q = op->apply((double2*)q_vec, (const double2*)t, na, 1))) return q;
+      } else if (fused) {
+        if ((q = dirac_kernel(c, t, p, na, m0, 0, oprec, st))) return q;
+        int nb = 0;
+        if ((q = dirac_bri_shiftdot(c, q_vec, t, na, m0, oprec, st, p, bsig.as<double>(), bpart_sd.as<double>(), &nb)))
+          return q;
+        k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, bpart_sd.as<double>(), nb); note_launch();
       } else {
         if ((q = dirac_kernel(c, t, p, na, m0, 0, oprec, st))) return q;
         if ((q = dirac_kernel(c, q_vec, t, na, m0, 1, oprec, st))) return q;
       }
-      k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q_vec, part); note_launch();
-      k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
-      k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (T*)x, part, it0 + j == 0 ? 1 : 0);
+      if (!fused || op) {
+        k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q_vec, part); note_launch();
+        k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+      }
+      if (x64)
+        k_update_fused<R, double2><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (double2*)x64, part,
+                                                                it0 + j == 0 ? 1 : 0);
+      else
+        k_update_fused<R><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (T*)x, part, it0 + j == 0 ? 1 : 0);
       note_launch();
       k_scalar_beta<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
       k_update_p0<R><<<vga, RED_THREADS, 0, st>>>(n2, S, r, p); note_launch();
@@ -856,6 +885,14 @@ int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
     if (rc) return rc;
     for (int s = 0; s < nrhs; ++s) rn2[(size_t)k * nrhs + s] = tmp[s];
   }
+  const bool rlog = getenv("BRI_REFINE_LOG") != nullptr;
+  if (rlog)
+    for (int k = 0; k < n; ++k) {
+      double worst = 0.0;
+      for (int s = 0; s < nrhs; ++s)
+        worst = std::max(worst, std::sqrt(rn2[(size_t)k * nrhs + s] / std::max(bn2[s], 1e-300)));
+      fprintf(stderr, "bri refine: shift %d sigma %.4e  relres after phase 1 %.3e\n", k, sig[k], worst);
+    }
   btmp1.reset();
   btmp2.reset();
   lap(1);
@@ -902,9 +939,17 @@ int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
       // Corrections always use FP32 links: with BF16 links the operator error
       // (~4e-3 relative) times the condition number of the small shifts
       // exceeds one, so a BF16 correction would not reduce the residual.
+      auto tc0 = std::chrono::steady_clock::now();
       rc = multishift_solve<float>(c, BRI_PREC_F32, m0, m, 1, msig.data(), brhs.as<float>(), bsol.as<float>(),
                                    1e-5, maxiter, &itc, &cnt, mtol.data());
       if (rc < 0) return rc;
+      if (rlog) {
+        cudaStreamSynchronize(st);
+        fprintf(stderr, "bri refine: round %d chunk of %d systems (slots %lld..%lld, tol %.2e..%.2e): %d iterations, %.3f s\n",
+                round, m, slots[0], slots[m - 1], *std::min_element(mtol.begin(), mtol.end()),
+                *std::max_element(mtol.begin(), mtol.end()), itc,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - tc0).count());
+      }
       // X += e (FP64); r -= (A + sigma) e with the FP32 operator
       if ((rc = bt1.alloc(sizeof(float) * nreal * m, st))) return rc;
       if ((rc = bt2.alloc(sizeof(float) * nreal * m, st))) return rc;
@@ -933,6 +978,7 @@ int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
         rn2[slot] = tmp[j];
         if (err_acc[slot] > 0.25 * goal && std::sqrt(rn2[slot]) <= goal) verify.push_back(slot);
       }
+      if (rlog) fprintf(stderr, "bri refine: round %d: %zu FP64 verifications\n", round, verify.size());
       if (!verify.empty()) {
         DevBuf v1, v2;
         if ((rc = v1.alloc(sizeof(double) * nreal, st))) return rc;
@@ -959,7 +1005,7 @@ int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
 // the host neither polls nor relaunches.  x = [system][shift][n2].
 template <typename R, typename LS>
 int batch_multishift(cudaStream_t st, const BatchTab& tab, const std::vector<SysDesc>& sdh, int nshift,
-                     const double* sig, const typename P2<R>::T* b, typename P2<R>::T* x, double tol, int maxiter,
+                     const double* sig, const typename P2<R>::T* b, double2* x, double tol, int maxiter,
                      int* iters_out, Counters* cnt, double* lam_out) {
   using T = typename P2<R>::T;
   const int S = (int)sdh.size();
@@ -1135,26 +1181,28 @@ int solve_shifts(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
     if (solve_rc < 0) return solve_rc;
     lap(0);
   } else if (prec == BRI_PREC_F32 || prec == BRI_PREC_F32_BF16) {
-    // phase 1: FP32 multi-shift (FP64 scalars and reductions)
-    DevBuf bb32, bx32;
+    // phase 1: FP32 multi-shift (FP64 scalars and reductions).  The shifted
+    // solutions accumulate in FP64, straight into X: rounded to FP32 they would
+    // carry an error that, times the condition number of the small shifts,
+    // dominates their true residual (2e-5 of ||b|| for the smallest shift of
+    // the 24^3 x 48 workload, against 8e-7 with FP64 accumulation).
+    DevBuf bb32;
     if ((rc = bb32.alloc(sizeof(float) * nreal * nrhs, st))) return rc;
-    if ((rc = bx32.alloc(sizeof(float) * nreal * nrhs * n, st))) return rc;
     k_convert<double, float><<<1024, 256, 0, st>>>(nreal * nrhs, b, bb32.as<float>()); note_launch();
     // The FP32 solve is run to 1e-7 (FP32 links) where the gap between its
-    // recursive and true residuals (~1e-7 of ||b||) stops further progress
-    // from helping the corrections; with BF16 links to 1e-6.
+    // recursive and true residuals (the FP32 operator's rounding, 3e-8 to
+    // 8e-7 of ||b|| from the largest to the smallest shift) stops further
+    // progress from helping the corrections; with BF16 links to 1e-6.
     const double tol1 = std::max(tol, prec == BRI_PREC_F32 ? 1e-7 : 1e-6);
     int it1 = 0;
     double lam_est = 0.0;
-    rc = multishift_solve<float>(c, prec, m0, nrhs, n, sig_all.data(), bb32.as<float>(), bx32.as<float>(), tol1,
-                                 maxiter, &it1, &cnt, nullptr, &lam_est);
+    rc = multishift_solve<float>(c, prec, m0, nrhs, n, sig_all.data(), bb32.as<float>(), nullptr, tol1, maxiter,
+                                 &it1, &cnt, nullptr, &lam_est, nullptr, X);
     lam_est = 1.1 * lam_est + 1e-3;
     if (rc < 0) return rc;
     iters = it1;
-    k_convert<float, double><<<1024, 256, 0, st>>>(nreal * nrhs * n, bx32.as<float>(), X); note_launch();
-    BRI_LAUNCH_CHECK("convert");
+    BRI_LAUNCH_CHECK("phase 1");
     bb32.reset();
-    bx32.reset();
     lap(0);
     solve_rc = refine_mixed(c, b, nrhs, n, sig, m0, tol, maxiter, X, lam_est, info, lap);
     if (solve_rc < 0) return solve_rc;
@@ -1372,14 +1420,14 @@ int batch_sign_apply(bri_ctx* const* cs, int nctx, void* const* ys, const void* 
     DevBuf bb, bx;
     int q;
     if ((q = bb.alloc(sizeof(T) * off, bs))) return q;
-    if ((q = bx.alloc(sizeof(T) * off * n, bs))) return q;
+    if ((q = bx.alloc(sizeof(double2) * off * n, bs))) return q;
     for (int i = 0; i < nctx; ++i) {
       kb_scatter_b<R><<<dim3(grid_for(cs[i]->g.V * 12, nrhs[i]), nrhs[i]), RED_THREADS, 0, bs>>>(
           bsd.as<SysDesc>(), first_sys[i], (const double2*)xs[i], bb.as<T>());
       note_launch();
     }
     const double tol1 = sizeof(R) == 8 ? tol : std::max(tol, prec == BRI_PREC_F32 ? 1e-7 : 1e-6);
-    q = batch_multishift<R, LS>(bs, tab, sd, n, sig, bb.as<T>(), bx.as<T>(), tol1, maxiter, &info1.iters, &info1.cnt,
+    q = batch_multishift<R, LS>(bs, tab, sd, n, sig, bb.as<T>(), bx.as<double2>(), tol1, maxiter, &info1.iters, &info1.cnt,
                                 &lam_est);
     if (q < 0) return q;
     solve_rc = std::max(solve_rc, q);
@@ -1387,8 +1435,8 @@ int batch_sign_apply(bri_ctx* const* cs, int nctx, void* const* ys, const void* 
       const int64_t nreal = cs[i]->g.V * 24;
       int qq;
       if ((qq = Xs[i].alloc(sizeof(double) * nreal * nrhs[i] * n, bs))) return qq;
-      kb_gather_x<R><<<dim3(grid_for(cs[i]->g.V * 12, nrhs[i] * n), nrhs[i], n), RED_THREADS, 0, bs>>>(
-          bsd.as<SysDesc>(), first_sys[i], nrhs[i], n, bx.as<T>(), Xs[i].as<double2>());
+      kb_gather_x<<<dim3(grid_for(cs[i]->g.V * 12, nrhs[i] * n), nrhs[i], n), RED_THREADS, 0, bs>>>(
+          bsd.as<SysDesc>(), first_sys[i], nrhs[i], n, bx.as<double2>(), Xs[i].as<double2>());
       note_launch();
     }
     BRI_LAUNCH_CHECK("batched phase 1");

@@ -33,9 +33,11 @@ std::mutex g_scratch_mu;
 
 // Bytes the FP64 solve needs: the n solution vectors, the n shifted search
 // directions and three work vectors per right-hand side (192 B per site each),
-// plus per-system solver state, reduction partials and alignment slack.
+// plus per-system solver state, reduction partials (those of the stencil's
+// fused epilogue: one per 64 sites) and alignment slack.
 size_t noalloc_need(int64_t V, int nrhs, int n) {
-  return size_t(192) * size_t(V) * size_t(nrhs) * size_t(2 * n + 3) + size_t(64) * 1024 + size_t(4096) * nrhs;
+  return size_t(192) * size_t(V) * size_t(nrhs) * size_t(2 * n + 3) + size_t(64) * 1024 + size_t(4096) * nrhs +
+         size_t(8) * size_t(nrhs) * size_t((V + 63) / 64) + 512;
 }
 
 }  // namespace

@@ -143,6 +143,16 @@ bool tune_lookup(const char* key, StencilConfig* out);
 void tune_store(const char* key, const StencilConfig& cf);
 std::mutex& tune_mutex();
 
+// Fused solver epilogue of a stencil launch: q = D x + sigma_s p_s at every
+// site, and per block the partial sums of Re<p_s, q> in FP64 (the inner
+// product of the multi-shift CG), written to part[s * blocks + site block] for
+// the launch's right-hand side s.  p has the spinors' layout.
+template <typename R> struct ShiftDot {
+  const R* p;          // base search directions p_s (nullptr: no epilogue)
+  const double* sig;   // per-system shift sigma_s
+  double* part;        // [nsys][site blocks]
+};
+
 // Grid of a stencil launch: the right-hand-side groups in x (fastest, so the
 // groups of one site block run together and reuse its links from L2) and the
 // site blocks in y, unless there are more site blocks than a grid's y extent
@@ -159,7 +169,7 @@ inline StencilGrid stencil_grid(int64_t site_blocks, int groups) {
 // Host-side launchers (one translation unit per precision).
 template <typename R, typename LS>
 int launch_bri_t(const Geom& g, R* y, const R* x, const LS* W, const R* cl, R diag, int nrhs, int dagger,
-                 cudaStream_t s);
+                 cudaStream_t s, const ShiftDot<R>* sd = nullptr, int* sd_blocks = nullptr);
 template <typename R, typename LS>
 int launch_wil_t(const Geom& g, R* y, const R* x, const LS* U, const R* cl, R diag, int nrhs, int dagger,
                  cudaStream_t s);

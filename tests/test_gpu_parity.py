@@ -283,3 +283,39 @@ def test_bri_apply_every_launch_configuration(force, monkeypatch):
         y = lat.bri_apply(torch.from_numpy(x).to(torch.complex64).cuda(), -1.0, dagger=dagger).cpu().numpy()
         want = op.apply_dagger(x) if dagger else op.apply(x)
         assert relerr(y, want) < 1e-5
+
+
+def test_zero_source_and_free_field():
+    """Degenerate inputs: a zero source among non-zero ones gives exactly zero (the solver stops that
+    system at its zero norm); on the free field (U = 1, where the clover term vanishes) the overlap
+    equals the oracle, whose free-field form is pinned to App. A's momentum-space expression."""
+    dims = RAGGED
+    u = sf.gauge_field(dims, 0, eps=0.0)
+    x = sf.gaussian_source(dims, 3, 1021)
+    x[1] = 0.0
+    lat = _lattice(dims, u, 1.0)
+    y, st = lat.overlap_apply(torch.from_numpy(x).cuda(), n=8, rho=1.0, tol=1e-13)
+    assert st["converged"]
+    got = y.cpu().numpy()
+    assert np.abs(got[1]).max() == 0.0
+    want, _ = overlap.overlap_apply(dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0), x, 1.0, 8, 1e-13)
+    assert relerr(got, want) < 1e-12
+
+
+def test_full_size_overlap_properties():
+    """The benchmark's workload size (24^3 x 48, stout-smeared field, c_SW = 1, KL order 16, mixed
+    precision): every shift's FP64 true residual reaches 1e-10, and D_ov is gamma5-hermitian,
+    <phi, D psi> = <gamma5 D gamma5 phi, psi>, to the accuracy of the solves."""
+    dims = (24, 24, 24, 48)
+    u = sf.gauge_field(dims, 1, 0.1, 3, device="cuda")
+    lat = _lattice(dims, u, 1.0)
+    phi = torch.from_numpy(sf.gaussian_source(dims, 1, 1031, normalize=True)).cuda()
+    psi = torch.from_numpy(sf.gaussian_source(dims, 1, 1032, normalize=True)).cuda()
+    g5 = torch.tensor([1.0, 1.0, -1.0, -1.0], dtype=torch.complex128, device="cuda").view(4, 1)
+    d_psi, st = lat.overlap_apply(psi, n=16, rho=1.0, tol=1e-10, prec=PREC_F32, want_true_residual=True)
+    assert st["converged"]
+    assert st["max_true_residual"] <= 1e-10
+    d_phi, _ = lat.overlap_apply((phi * g5).contiguous(), n=16, rho=1.0, tol=1e-10, prec=PREC_F32)
+    lhs = torch.vdot(phi.flatten(), d_psi.flatten())
+    rhs = torch.vdot((d_phi * g5).flatten(), psi.flatten())
+    assert abs((lhs - rhs).item()) <= 1e-8 * max(abs(lhs.item()), 1.0)
