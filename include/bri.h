@@ -18,8 +18,9 @@
  *   gauge U   = [V][mu=0..3 (x,y,z,t)][3][3] complex128 (re, im interleaved),
  *               device memory; U_mu(n) transports from n+mu to n.
  *   spinors   = [rhs][V][spin 4][colour 3] complex, interleaved (re, im), device
- *               memory, complex128 when the precision is BRI_PREC_F64 and
- *               complex64 (float) for BRI_PREC_F32 / BRI_PREC_F32_BF16.
+ *               memory, complex128 when the precision is BRI_PREC_F64 (or
+ *               BRI_PREC_DW) and complex64 (float) for BRI_PREC_F32 /
+ *               BRI_PREC_F32_BF16.
  *   gamma basis: chiral, gamma_k = [[0,-i s_k],[i s_k,0]], gamma_4 = [[0,1],[1,0]],
  *               gamma5 = diag(1,1,-1,-1) (App. C counts gamma products as free
  *               permutations in this basis).
@@ -55,6 +56,9 @@ extern "C" {
 #define BRI_PREC_F64 0       /* complex128 spinors, FP64 links, FP64 arithmetic */
 #define BRI_PREC_F32 1       /* complex64 spinors, FP32 links, FP32 accumulation */
 #define BRI_PREC_F32_BF16 2  /* complex64 spinors, BF16-stored links, FP32 accumulation */
+#define BRI_PREC_DW 3        /* bri_apply only: complex128 spinors in and out, the FP64 links and clover
+                                split into double-word FP32 pairs, double-word FP32 arithmetic
+                                (error-free transformations: ~48-bit significands on the FP32 pipe) */
 
 /* bri_create flags */
 #define BRI_ANTIPERIODIC_T 1 /* antiperiodic time direction (sign of U_t on the last slice) */
@@ -118,8 +122,13 @@ int bri_get_links(bri_ctx* ctx, double* W);
 /* y = D_bri x (dagger = 0) or D_bri^dagger x = gamma5 D_bri gamma5 x
  * (dagger = 1) for nrhs right-hand sides, at bare mass m0 (Eq. def_bril;
  * App. C: y(n) = sum over the 81 offsets of W_d(n) M_d x(n+d) with real
- * stencil weights).  prec selects spinor dtype and link storage.  x and y
- * must not alias. */
+ * stencil weights).  prec selects spinor dtype and link storage; with
+ * BRI_PREC_DW (complex128 in and out) the operator runs in double-word FP32
+ * arithmetic (relative error ~1e-15, the FP64 operator's accuracy class) and
+ * the call allocates two double-word work vectors of nrhs right-hand sides
+ * (stream-ordered) plus, on first use after bri_build_links, the double-word
+ * link and clover copies (5760 + 576 bytes per site).  x and y must not
+ * alias. */
 int bri_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, double m0, int dagger, int prec);
 
 /* y = D_wil x or D_wil^dagger x (Eq. def_wils): 9-point stencil over the thin

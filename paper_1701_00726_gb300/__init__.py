@@ -16,11 +16,11 @@ import ctypes
 
 from . import _lib
 from ._lib import (ANTIPERIODIC_T, BRI_NOT_CONVERGED, KERNEL_BRILLOUIN, KERNEL_WILSON, KL_DIAGONAL, KL_UPPER,
-                   PREC_F32, PREC_F32_BF16, PREC_F64, BriError, BriStats, dispersion, kl_coeffs)
+                   PREC_DW, PREC_F32, PREC_F32_BF16, PREC_F64, BriError, BriStats, dispersion, kl_coeffs)
 
 __all__ = ["Lattice", "overlap", "OverlapFunction", "overlap_apply_batch", "kl_coeffs", "dispersion", "BriError",
            "BriStats",
-           "PREC_F64", "PREC_F32", "PREC_F32_BF16", "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T", "KERNEL_BRILLOUIN",
+           "PREC_F64", "PREC_F32", "PREC_F32_BF16", "PREC_DW", "KL_DIAGONAL", "KL_UPPER", "ANTIPERIODIC_T", "KERNEL_BRILLOUIN",
            "KERNEL_WILSON"]
 
 
@@ -119,12 +119,17 @@ class Lattice:
             return PREC_F64
         return PREC_F32_BF16 if bf16_links else PREC_F32
 
-    def bri_apply(self, x, m0, dagger=False, bf16_links=False, out=None):
+    def bri_apply(self, x, m0, dagger=False, bf16_links=False, out=None, double_word=False):
+        """y = D_bri x (or D^dagger x).  complex128 x: FP64, or with double_word=True the double-word
+        FP32 operator (FP64-class accuracy on the FP32 pipe); complex64 x: FP32 (or BF16-stored) links."""
         torch = _torch()
         nrhs = self._spinor(x, (torch.complex128, torch.complex64))
+        if double_word and x.dtype != torch.complex128:
+            raise BriError("bri_apply: the double-word operator takes complex128 spinors")
         y = torch.empty_like(x) if out is None else out
+        prec = PREC_DW if double_word else self._prec_for(x, bf16_links)
         _lib.check(self.lib.bri_apply(self._h, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
-                                      float(m0), int(bool(dagger)), self._prec_for(x, bf16_links)), "bri_apply")
+                                      float(m0), int(bool(dagger)), prec), "bri_apply")
         return y
 
     def wils_apply(self, x, m0, dagger=False, out=None):

@@ -19,6 +19,7 @@ BRI_NOT_CONVERGED = 1
 PREC_F64 = 0
 PREC_F32 = 1
 PREC_F32_BF16 = 2
+PREC_DW = 3  # bri_apply only: complex128 in/out, double-word FP32 arithmetic
 ANTIPERIODIC_T = 1
 KERNEL_BRILLOUIN = 0
 KERNEL_WILSON = 1

@@ -180,6 +180,8 @@ void bri_destroy(bri_ctx* c) {
   cudaFree(c->U32);
   cudaFree(c->C64);
   cudaFree(c->C32);
+  cudaFree(c->Wdw);
+  cudaFree(c->Cdw);
   for (auto& r : c->prof_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -240,7 +242,8 @@ int bri_get_links(bri_ctx* c, double* W) {
   return launch_export_links(c, W);
 }
 
-static int check_apply(bri_ctx* c, void* y, const void* x, int nrhs, int prec, const char* who) {
+static int check_apply(bri_ctx* c, void* y, const void* x, int nrhs, int prec, const char* who,
+                       bool allow_dw = false) {
   if (!c || !y || !x) {
     set_error(std::string(who) + ": null argument");
     return BRI_ERR_INVALID;
@@ -253,7 +256,8 @@ static int check_apply(bri_ctx* c, void* y, const void* x, int nrhs, int prec, c
     set_error(std::string(who) + ": nrhs must be in [1, 65535]");
     return BRI_ERR_INVALID;
   }
-  if (prec != BRI_PREC_F64 && prec != BRI_PREC_F32 && prec != BRI_PREC_F32_BF16) {
+  if (prec != BRI_PREC_F64 && prec != BRI_PREC_F32 && prec != BRI_PREC_F32_BF16 &&
+      !(allow_dw && prec == BRI_PREC_DW)) {
     set_error(std::string(who) + ": unknown precision");
     return BRI_ERR_INVALID;
   }
@@ -269,9 +273,21 @@ static int check_apply(bri_ctx* c, void* y, const void* x, int nrhs, int prec, c
 }
 
 int bri_apply(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec) {
-  int rc = check_apply(c, y, x, nrhs, prec, "bri_apply");
+  int rc = check_apply(c, y, x, nrhs, prec, "bri_apply", true);
   if (rc) return rc;
-  return dirac_bri(c, y, x, nrhs, m0, dagger ? 1 : 0, prec, c->stream);
+  if (prec != BRI_PREC_DW) return dirac_bri(c, y, x, nrhs, m0, dagger ? 1 : 0, prec, c->stream);
+  void* tmp = nullptr;
+  const size_t bytes = sizeof(float4) * 2 * (size_t)c->g.V * 12 * nrhs;
+  cudaError_t e = cudaMallocAsync(&tmp, bytes, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("bri_apply: cudaMallocAsync failed: ") + cudaGetErrorString(e));
+    return BRI_ERR_OOM;
+  }
+  note_device_alloc();
+  rc = dirac_bri_dw64(c, (double*)y, (const double*)x, nrhs, m0, dagger ? 1 : 0, tmp, c->stream);
+  cudaFreeAsync(tmp, c->stream);
+  return rc;
 }
 
 int wils_apply(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec) {

@@ -273,6 +273,117 @@ __global__ void __launch_bounds__(128, 4)
   }
 }
 
+// Two right-hand sides per thread on the paired pipe: the links of a hop pair
+// (and their broadcast pairs) are loaded once and used for both; the grid's
+// groups are rhs pairs (rhs0 + 2 grp, rhs0 + 2 grp + 1).
+template <typename LS, bool EPI>
+__global__ void __launch_bounds__(128, 3)
+    bri_kernel_c2x2(Geom g, float* __restrict__ y, const float* __restrict__ x, const LS* __restrict__ W,
+                    const float* __restrict__ cl, float diag, int rhs0, int gfirst,
+                    const __grid_constant__ HopTableC2 H, ShiftDot<float> sd) {
+  const int grp = gfirst ? blockIdx.x : blockIdx.y, blk = gfirst ? blockIdx.y : blockIdx.x;
+  const int n0 = blk * blockDim.x + threadIdx.x;
+  if (!EPI && n0 >= g.V) return;
+  const bool valid = n0 < g.V;
+  const int n = valid ? n0 : 0;
+  const int V = (int)g.V;
+  const int64_t rstride = g.V * 24;
+  const int s0 = rhs0 + 2 * grp;
+  const int64_t roff = (int64_t)s0 * rstride;
+  const float* xin0 = x + roff;
+  const float* xin1 = xin0 + rstride;
+  int co[4], L[4], str[4];
+  {
+    int r = n;
+#pragma unroll
+    for (int mu = 0; mu < 3; ++mu) {
+      co[mu] = r % g.L[mu];
+      r /= g.L[mu];
+    }
+    co[3] = r;
+  }
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    L[mu] = g.L[mu];
+    str[mu] = (int)g.str[mu];
+  }
+  float2 acc0[4][3], acc1[4][3];
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int aa = 0; aa < 3; ++aa) {
+      acc0[sp][aa] = make_float2(0.f, 0.f);
+      acc1[sp][aa] = make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+  for (int j = 0; j < 40; ++j) {
+    int mp = 0, mm = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int d = H.site_d[j][mu];
+      mp += wrap(co[mu] + d, L[mu]) * str[mu];
+      mm += wrap(co[mu] - d, L[mu]) * str[mu];
+    }
+    C<float> w[3][3], wm[3][3];
+    load_stored_link<float, LS>(w, W, j, n, V);
+    load_stored_link<float, LS>(wm, W, j, mm, V);
+    c2_pair(acc0, xin0, mp, mm, w, wm, H.k[j]);
+    c2_pair(acc1, xin1, mp, mm, w, wm, H.k[j]);
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float* xr = r ? xin1 : xin0;
+    const float2(&acc)[4][3] = r ? acc1 : acc0;
+    const int64_t ro = roff + r * rstride;
+    Spinor<float> xc, out;
+    load_spinor(xc, xr + (int64_t)n * 24);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        out.v[sp][aa].re = fmaf(diag, xc.v[sp][aa].re, acc[sp][aa].x);
+        out.v[sp][aa].im = fmaf(diag, xc.v[sp][aa].im, acc[sp][aa].y);
+      }
+    if (cl) add_clover(out, xc, cl, g.V, n);
+    if constexpr (EPI) {
+      const int s = s0 + r;
+      const float sg = (float)sd.sig[s];
+      Spinor<float> pv;
+      load_spinor(pv, sd.p + ro + (int64_t)n * 24);
+      float dt = 0.f;
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa) {
+          out.v[sp][aa].re = fmaf(sg, pv.v[sp][aa].re, out.v[sp][aa].re);
+          out.v[sp][aa].im = fmaf(sg, pv.v[sp][aa].im, out.v[sp][aa].im);
+          dt = fmaf(pv.v[sp][aa].re, out.v[sp][aa].re, dt);
+          dt = fmaf(pv.v[sp][aa].im, out.v[sp][aa].im, dt);
+        }
+      if (valid) store_spinor(y + ro + (int64_t)n * 24, out);
+      const double t = block_total_c2(valid ? (double)dt : 0.0);
+      if (threadIdx.x == 0) sd.part[(int64_t)s * (gfirst ? gridDim.y : gridDim.x) + blk] = t;
+    } else {
+      store_spinor(y + ro + (int64_t)n * 24, out);
+    }
+  }
+}
+
+template <typename LS>
+inline void launch_bri_c2x2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
+                            int dagger, int rhs0, int npairs, int threads, cudaStream_t s,
+                            const ShiftDot<float>* sd = nullptr) {
+  const StencilGrid sg = stencil_grid(blocks_for(g.V, threads), npairs);
+  if (sd)
+    bri_kernel_c2x2<LS, true><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, sg.gfirst,
+                                                          hop_table_c2(dagger), *sd);
+  else
+    bri_kernel_c2x2<LS, false><<<sg.grid, threads, 0, s>>>(g, y, x, W, cl, diag, rhs0, sg.gfirst,
+                                                           hop_table_c2(dagger),
+                                                           ShiftDot<float>{nullptr, nullptr, nullptr});
+  note_launch();
+}
+
 template <typename LS>
 inline void launch_bri_c2(const Geom& g, float* y, const float* x, const LS* W, const float* cl, float diag,
                           int dagger, int rhs0, int nrhs, int threads, cudaStream_t s,

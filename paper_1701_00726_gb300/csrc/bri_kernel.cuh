@@ -281,6 +281,10 @@ inline void launch_with(const StencilConfig& cf, const Geom& g, R* y, const R* x
     } else if (cf.pairs == 2) {
       launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs, cf.threads, s, sd);
       done = nrhs;
+    } else if (cf.pairs == 3) {  // two rhs per thread on the paired pipe, an odd one on the one-rhs kernel
+      if (nrhs >= 2) launch_bri_c2x2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, 0, nrhs / 2, cf.threads, s, sd);
+      if (nrhs % 2) launch_bri_c2<LS>(g, y, x, W, cl, diag, sgn < 0 ? 1 : 0, nrhs - 1, 1, cf.threads, s, sd);
+      done = nrhs;
     } else if (nrhs >= 2 && cf.pairs) {
       launch_bri_nr<R, LS, 2>(g, y, x, W, cl, diag, sgn, 0, nrhs / 2, cf.threads, s, sd);
       done = (nrhs / 2) * 2;
@@ -299,7 +303,7 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
   StencilConfig def;
   if (const char* f = getenv("BRI_STENCIL_FORCE")) {  // "pairs,threads,rg", read on every launch
     StencilConfig cf;
-    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && cf.pairs >= 0 && cf.pairs <= 2 &&
+    if (sscanf(f, "%d,%d,%d", &cf.pairs, &cf.threads, &cf.rg) == 3 && cf.pairs >= 0 && cf.pairs <= 3 &&
         (cf.threads == 64 || cf.threads == 128) && (cf.rg == 1 || cf.rg == 2 || cf.rg == 4))
       return cf;
   }
@@ -327,6 +331,8 @@ StencilConfig tuned_config(const Geom& g, R* y, const R* x, const LS* W, const R
     for (int th : {64, 128}) cands.push_back(StencilConfig{pairs, th, 1});
   if (sizeof(R) == 4)
     for (int th : {64, 128}) cands.push_back(StencilConfig{2, th, 1});
+  if (sizeof(R) == 4 && nrhs >= 2)
+    for (int th : {64, 128}) cands.push_back(StencilConfig{3, th, 1});
   if (sizeof(R) == 4 && nrhs >= 2) cands.push_back(StencilConfig{0, 128, 2});
   if (sizeof(R) == 4 && nrhs >= 4) cands.push_back(StencilConfig{0, 128, 4});
   cudaEvent_t e0, e1;

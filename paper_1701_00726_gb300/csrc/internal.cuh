@@ -80,6 +80,12 @@ struct bri_ctx {
   // [block][36][V]: 6 diagonal reals, then 15 upper off-diagonal complex.
   double* C64 = nullptr;
   float* C32 = nullptr;
+  // Double-word FP32 copies (h, l) of W64 and C64 for the FP64-class stencil
+  // on the FP32 pipe: [40][9][V] float4 and [2][36][V] float2, made on first
+  // use after each bri_build_links (dw_valid).
+  void* Wdw = nullptr;
+  void* Cdw = nullptr;
+  bool dw_valid = false;
   // solver workspace (grown on demand)
   bri::Workspace ws;
   bri::Workspace ws_small;
@@ -117,6 +123,16 @@ int dirac_bri(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagge
 int dirac_wil(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, int prec,
               cudaStream_t s);
 // The solver's fused D^dagger application: y = D^dagger x + sigma_s p_s and the
+// Double-word FP32 Brillouin stencil (bri_dw.cu): y = D x or D^dagger x on
+// double-word vectors ([nrhs][V][12] float4), FP64 in and out through the
+// split/join kernels (tmp: two double-word vectors of nrhs right-hand sides),
+// and the normal operator D^dagger D on FP64 vectors (t1, t2 double-word
+// scratch; t2 may be out).
+int ensure_dw_links(bri_ctx* c);
+int dirac_bri_dw(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int dagger, cudaStream_t s);
+int dirac_bri_dw64(bri_ctx* c, double* y, const double* x, int nrhs, double m0, int dagger, void* tmp,
+                   cudaStream_t s);
+int normal_op_dw(bri_ctx* c, double* out, const double* x, int nrhs, double m0, void* t1, void* t2, cudaStream_t s);
 // per-site-block partials of Re<p_s, y> (Brillouin kernel only); sd_blocks
 // receives the number of partials per system (part: [nrhs][sd_blocks]).
 int dirac_bri_shiftdot(bri_ctx* c, void* y, const void* x, int nrhs, double m0, int prec, cudaStream_t s,

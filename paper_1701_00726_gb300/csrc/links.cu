@@ -305,6 +305,7 @@ int launch_build_links(bri_ctx* c, const double* U, double c_sw) {
   narrow_links_kernel<<<blocks_for(360 * V, 256), 256, 0, st>>>(360 * V, c->W64, c->W32, c->W16, V); note_launch();
   BRI_LAUNCH_CHECK("narrow_links_kernel");
   c->have_clover = false;
+  c->dw_valid = false;
   c->c_sw = c_sw;
   if (c_sw != 0.0) {
     if ((rc = alloc((void**)&c->C64, sizeof(double) * 72 * V))) return rc;

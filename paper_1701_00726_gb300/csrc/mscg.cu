@@ -61,6 +61,19 @@ struct MsState {
   int nshift, done, iters, maxiter, error;
 };
 
+// Deferred shifted updates (FP32 solves): the coefficients of up to DW
+// iterations, recorded by k_scalar_alpha, and applied in one pass over the
+// shifted vectors by k_flush_shifts (residuals of those iterations kept in a
+// ring of DW vectors).  Step m of the window is iteration first_iter + m.
+constexpr int DW = 4;
+struct ShiftHist {
+  int n;         // recorded steps not yet applied
+  int first[DW]; // the step is the solve's first iteration (p_i = b, no direction update)
+  float z[DW][NS], b[DW][NS];
+  double a[DW][NS];
+  unsigned char act[DW][NS];
+};
+
 template <typename R> struct P2;
 template <> struct P2<float> { using T = float2; };
 template <> struct P2<double> { using T = double2; };
@@ -190,6 +203,109 @@ __global__ void k_update_fused(int64_t n2, int nsys, const MsState* __restrict__
   if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
 }
 
+// Per-iteration part of the deferred scheme (FP32 solves): r_j goes to the
+// ring slot of this step, x_0 += alpha_0 p_0 (FP64), r -= alpha q and the
+// partial ||r||^2.  The shifted directions and solutions wait for
+// k_flush_shifts.
+__global__ void k_update_base(int64_t n2, int nsys, const MsState* __restrict__ st,
+                              const ShiftHist* __restrict__ hist, const float2* __restrict__ q, float2* r,
+                              const float2* __restrict__ p, double2* x, float2* ring, double* part) {
+  const int s = blockIdx.y;
+  if (st[s].done) return;
+  const float alpha = (float)st[s].alpha;
+  const double a0 = st[s].a_s[0];
+  const int m = hist[s].n - 1;
+  float2* rs = ring + ((int64_t)m * nsys + s) * n2;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 rv = r[s * n2 + i];
+    rs[i] = rv;
+    const float2 pv = p[s * n2 + i];
+    double2 xv = x[s * n2 + i];
+    xv.x = fma(a0, (double)pv.x, xv.x);
+    xv.y = fma(a0, (double)pv.y, xv.y);
+    x[s * n2 + i] = xv;
+    const float2 qv = q[s * n2 + i];
+    rv.x = fmaf(-alpha, qv.x, rv.x);
+    rv.y = fmaf(-alpha, qv.y, rv.y);
+    r[s * n2 + i] = rv;
+    acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+  }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// The recorded steps of every shift i > 0 in one pass: for each step m (in
+// order) p_i = zeta_i r_m + beta_i p_i (not on the first iteration), then
+// x_i += alpha_i p_i -- the arithmetic of k_update_fused, step by step, with
+// p_i and x_i read and written once per window instead of once per step.
+// Called while the system may already be done (its last steps still pending).
+__global__ void k_flush_shifts(int64_t n2, int nsys, ShiftHist* hist, const float2* __restrict__ ring, float2* p,
+                               double2* x) {
+  const int s = blockIdx.y;
+  __shared__ float sz[DW][NS], sb[DW][NS];
+  __shared__ double sa[DW][NS];
+  __shared__ unsigned char sact[DW][NS];
+  __shared__ int sk[NS], snk, sn, sfirst[DW];
+  if (threadIdx.x == 0) {
+    const ShiftHist& h = hist[s];
+    const int nst = h.n;
+    int mk = 0;
+    for (int k = 1; k < NS; ++k) {
+      int any = 0;
+      for (int m = 0; m < nst; ++m) any |= h.act[m][k];
+      if (any) sk[mk++] = k;
+    }
+    for (int m = 0; m < nst; ++m) {
+      sfirst[m] = h.first[m];
+      for (int j = 0; j < mk; ++j) {
+        const int k = sk[j];
+        sz[m][j] = h.z[m][k];
+        sb[m][j] = h.b[m][k];
+        sa[m][j] = h.a[m][k];
+        sact[m][j] = h.act[m][k];
+      }
+    }
+    snk = mk;
+    sn = nst;
+  }
+  __syncthreads();
+  const int nk = snk, nst = sn;
+  if (nst > 0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+      float2 rv[DW];
+#pragma unroll
+      for (int m = 0; m < DW; ++m)
+        if (m < nst) rv[m] = ring[((int64_t)m * nsys + s) * n2 + i];
+      for (int j = 0; j < nk; ++j) {
+        const int64_t o = ((int64_t)sk[j] * nsys + s) * n2 + i;
+        float2 pv = p[o];
+        double2 xv = x[o];
+#pragma unroll
+        for (int m = 0; m < DW; ++m) {
+          if (m >= nst || !sact[m][j]) continue;
+          if (!sfirst[m]) {
+            const float z = sz[m][j], bt = sb[m][j];
+            pv.x = fmaf(bt, pv.x, z * rv[m].x);
+            pv.y = fmaf(bt, pv.y, z * rv[m].y);
+          }
+          const double a = sa[m][j];
+          xv.x = fma(a, (double)pv.x, xv.x);
+          xv.y = fma(a, (double)pv.y, xv.y);
+        }
+        p[o] = pv;
+        x[o] = xv;
+      }
+    }
+  }
+}
+
+// The window is applied: start the next one (a kernel of its own, after every
+// block of k_flush_shifts has read the history).
+__global__ void k_hist_reset(ShiftHist* hist, int nsys) {
+  for (int s = threadIdx.x; s < nsys; s += blockDim.x) hist[s].n = 0;
+}
+
 // p_0 = r + beta p_0 (base direction, zeta_0 = 1)
 template <typename R>
 __global__ void k_update_p0(int64_t n2, const MsState* __restrict__ st, const typename P2<R>::T* __restrict__ r,
@@ -233,7 +349,7 @@ __global__ void k_scalar_init(MsState* st, const double* part, int nblk) {
   }
 }
 
-__global__ void k_scalar_alpha(MsState* st, const double* part, int nblk) {
+__global__ void k_scalar_alpha(MsState* st, const double* part, int nblk, ShiftHist* hist = nullptr) {
   const int s = blockIdx.x;
   if (st[s].done) return;
   double acc = 0.0;
@@ -260,6 +376,17 @@ __global__ void k_scalar_alpha(MsState* st, const double* part, int nblk) {
       const double zn = S.zeta[k] * S.zeta_prev[k] * S.alpha_prev / den;
       S.zeta_next[k] = zn;
       S.a_s[k] = alpha * zn / S.zeta[k];
+    }
+    if (hist) {  // the coefficients this iteration's shifted update (i > 0) uses
+      ShiftHist& h = hist[s];
+      const int m = h.n++;
+      h.first[m] = S.iters == 0;
+      for (int k = 0; k < S.nshift; ++k) {
+        h.act[m][k] = (k > 0 && S.active[k]) ? 1 : 0;
+        h.z[m][k] = (float)S.zeta[k];
+        h.b[m][k] = (float)S.b_s[k];
+        h.a[m][k] = S.a_s[k];
+      }
     }
   }
 }
@@ -350,6 +477,16 @@ __global__ void k_residual(int64_t n, const double* __restrict__ b, const double
     if (res) res[o] = v;
     acc += v * v;
   }
+  double t = block_sum(acc);
+  if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
+}
+
+// partials of Re<a_s, b_s> (FP64)
+__global__ void k_dot_re(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* part) {
+  const int s = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[s * n + i] * b[s * n + i];
   double t = block_sum(acc);
   if (threadIdx.x == 0) part[s * gridDim.x + blockIdx.x] = t;
 }
@@ -696,6 +833,17 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
   // and the partials of Re<p_0, q> come out of the stencil's epilogue, so
   // k_shift_dot's pass over q and p_0 is not needed.
   const bool fused = op == nullptr && c->kernel == BRI_KERNEL_BRILLOUIN;
+  // Deferred shifted updates (FP32 solve with FP64 solutions): the shifted
+  // directions and solutions are advanced every DW iterations from a ring of
+  // the residuals of those iterations (same arithmetic, fewer passes).
+  const bool defer = sizeof(R) == 4 && x64 != nullptr;
+  DevBuf bring, bhist;
+  if (defer) {
+    if ((rc = bring.alloc(sizeof(T) * n2 * nsys * DW, st))) return rc;
+    if ((rc = bhist.alloc(sizeof(ShiftHist) * nsys, st))) return rc;
+    BRI_CUDA(cudaMemsetAsync(bhist.p, 0, sizeof(ShiftHist) * nsys, st));
+  }
+  ShiftHist* hist = defer ? bhist.as<ShiftHist>() : nullptr;
   DevBuf bsig, bpart_sd;
   std::vector<double> hsig(nsys);
   for (int s = 0; s < nsys; ++s) hsig[s] = hs[s].sig_base;
@@ -736,16 +884,19 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
         int nb = 0;
         if ((q = dirac_bri_shiftdot(c, q_vec, t, na, m0, oprec, st, p, bsig.as<double>(), bpart_sd.as<double>(), &nb)))
           return q;
-        k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, bpart_sd.as<double>(), nb); note_launch();
+        k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, bpart_sd.as<double>(), nb, hist); note_launch();
       } else {
         if ((q = dirac_kernel(c, t, p, na, m0, 0, oprec, st))) return q;
         if ((q = dirac_kernel(c, q_vec, t, na, m0, 1, oprec, st))) return q;
       }
       if (!fused || op) {
         k_shift_dot<R><<<vga, RED_THREADS, 0, st>>>(n2, S, p, q_vec, part); note_launch();
-        k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
+        k_scalar_alpha<<<na, RED_THREADS, 0, st>>>(S, part, nblk, hist); note_launch();
       }
-      if (x64)
+      if (defer)
+        k_update_base<<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, hist, (const float2*)q_vec, (float2*)r,
+                                                   (const float2*)p, (double2*)x64, (float2*)bring.p, part);
+      else if (x64)
         k_update_fused<R, double2><<<vga, RED_THREADS, 0, st>>>(n2, nsys, S, q_vec, r, p, (double2*)x64, part,
                                                                 it0 + j == 0 ? 1 : 0);
       else
@@ -753,6 +904,12 @@ int multishift_solve(bri_ctx* c, int prec, double m0, int nsys, int nshift, cons
       note_launch();
       k_scalar_beta<<<na, RED_THREADS, 0, st>>>(S, part, nblk); note_launch();
       k_update_p0<R><<<vga, RED_THREADS, 0, st>>>(n2, S, r, p); note_launch();
+      if (defer && ((j + 1) % DW == 0 || j == count - 1)) {
+        k_flush_shifts<<<vga, RED_THREADS, 0, st>>>(n2, nsys, hist, (const float2*)bring.p, (float2*)p,
+                                                    (double2*)x64);
+        note_launch();
+        k_hist_reset<<<1, 64, 0, st>>>(hist, na); note_launch();
+      }
     }
     return BRI_OK;
   };
@@ -848,6 +1005,56 @@ int residual64(bri_ctx* c, double m0, int nsys, const double* b, const double* X
   return BRI_OK;
 }
 
+// The same residual with A = D^dagger D applied in double-word FP32 arithmetic
+// (Brillouin kernel, bri_dw.cu): FP64-class accuracy on the FP32 pipe.
+int residual_dw(bri_ctx* c, double m0, int nsys, const double* b, const double* X, double sigma, double* res,
+                double* tmp1, double* tmp2, double* part, double* dsum, double* hsum, Counters* cnt) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->g.V * 24;
+  int rc = normal_op_dw(c, tmp2, X, nsys, m0, tmp1, tmp2, st);
+  if (rc) return rc;
+  cnt->matvecs += 2;
+  const int nblk = grid_for(n / 2, nsys);
+  k_residual<<<dim3(nblk, nsys), RED_THREADS, 0, st>>>(n, b, tmp2, X, sigma, res, part); note_launch();
+  k_sum_partials<<<nsys, RED_THREADS, 0, st>>>(part, nblk, dsum); note_launch();
+  BRI_LAUNCH_CHECK("residual_dw");
+  BRI_CUDA(cudaMemcpyAsync(hsum, dsum, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  BRI_CUDA(cudaStreamSynchronize(st));
+  return BRI_OK;
+}
+
+// ||X_s||^2 per system (FP64)
+int norms64(bri_ctx* c, int nsys, const double* X, double* part, double* dsum, double* hsum) {
+  cudaStream_t st = c->stream;
+  const int64_t n = c->g.V * 24;
+  const int nblk = grid_for(n / 2, nsys);
+  k_residual<<<dim3(nblk, nsys), RED_THREADS, 0, st>>>(n, X, X, X, -1.0, nullptr, part); note_launch();
+  k_sum_partials<<<nsys, RED_THREADS, 0, st>>>(part, nblk, dsum); note_launch();
+  BRI_LAUNCH_CHECK("norms64");
+  BRI_CUDA(cudaMemcpyAsync(hsum, dsum, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+  BRI_CUDA(cudaStreamSynchronize(st));
+  return BRI_OK;
+}
+
+// Bound on the error of the double-word normal operator relative to the norm
+// of its argument, ||A_dw x - A x|| <= kDwRelErr ||x||.  The inputs are split
+// to ~2^-49 of each component, the products and sums are error-free up to the
+// second word (~2^-48 of the terms, which cancel in D x), and the intermediate
+// D x is stored as a double-word pair.  Measured against the FP64 operator on
+// the 24^3 x 48 stout-smeared field: 2.5e-14 ||x|| for Gaussian x, 3.7e-14
+// ||x|| for a smooth x (the low-mode shape of the small shifts' solutions);
+// the bound takes 1e-13.
+constexpr double kDwRelErr = 1e-13;
+
+// The double-word residual serves a shift when its error bound stays below 5 %
+// of the target for every right-hand side: kDwRelErr ||X_s|| <= 0.05 tol ||b_s||.
+bool dw_residual_ok(const bri_ctx* c, const double* xn2, const double* bn2, int nsys, double tol) {
+  if (c->kernel != BRI_KERNEL_BRILLOUIN) return false;
+  for (int s = 0; s < nsys; ++s)
+    if (kDwRelErr * std::sqrt(xn2[s]) > 0.05 * tol * std::sqrt(bn2[s])) return false;
+  return true;
+}
+
 // Phases 2 and 3 of the mixed scheme for X = the FP32 multi-shift solution
 // (converted to FP64): one FP64 residual per (shift, rhs), then batched FP32
 // CG corrections of every shift still above tol, with the FP32-tracked
@@ -878,20 +1085,48 @@ int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
   k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_r, bdsum.as<double>()); note_launch();
   BRI_CUDA(cudaMemcpyAsync(bn2.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   BRI_CUDA(cudaStreamSynchronize(st));
+  // Each shift's residual in double-word arithmetic where its error bound
+  // allows (||X_k|| small enough against tol ||b||), else in FP64.
+  std::vector<double> xn2((size_t)n * nrhs);
+  std::vector<char> dw_slot((size_t)n * nrhs, 0);
   for (int k = 0; k < n; ++k) {
-    rc = residual64(c, m0, nrhs, b, X + (int64_t)k * nrhs * nreal, sig[k],
-                    bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(), btmp2.as<double>(),
-                    bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+    const double* Xk = X + (int64_t)k * nrhs * nreal;
+    if ((rc = norms64(c, nrhs, Xk, bpart.as<double>(), bdsum.as<double>(), tmp.data()))) return rc;
+    for (int s = 0; s < nrhs; ++s) xn2[(size_t)k * nrhs + s] = tmp[s];
+    const bool dw = dw_residual_ok(c, tmp.data(), bn2.data(), nrhs, tol);
+    for (int s = 0; s < nrhs; ++s) dw_slot[(size_t)k * nrhs + s] = dw;
+    if (dw)
+      rc = residual_dw(c, m0, nrhs, b, Xk, sig[k], bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(),
+                       btmp2.as<double>(), bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+    else
+      rc = residual64(c, m0, nrhs, b, Xk, sig[k], bres.as<double>() + (int64_t)k * nrhs * nreal, btmp1.as<double>(),
+                      btmp2.as<double>(), bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
     if (rc) return rc;
     for (int s = 0; s < nrhs; ++s) rn2[(size_t)k * nrhs + s] = tmp[s];
   }
   const bool rlog = getenv("BRI_REFINE_LOG") != nullptr;
   if (rlog)
     for (int k = 0; k < n; ++k) {
-      double worst = 0.0;
-      for (int s = 0; s < nrhs; ++s)
+      double worst = 0.0, xmax = 0.0;
+      for (int s = 0; s < nrhs; ++s) {
         worst = std::max(worst, std::sqrt(rn2[(size_t)k * nrhs + s] / std::max(bn2[s], 1e-300)));
-      fprintf(stderr, "bri refine: shift %d sigma %.4e  relres after phase 1 %.3e\n", k, sig[k], worst);
+        xmax = std::max(xmax, std::sqrt(xn2[(size_t)k * nrhs + s] / std::max(bn2[s], 1e-300)));
+      }
+      // alignment of this shift's residual with the base shift's (per rhs, worst)
+      const int nblk_c = grid_for(nreal / 2, nrhs);
+      k_dot_re<<<dim3(nblk_c, nrhs), RED_THREADS, 0, st>>>(nreal, bres.as<double>(),
+                                                           bres.as<double>() + (int64_t)k * nrhs * nreal,
+                                                           bpart.as<double>());
+      k_sum_partials<<<nrhs, RED_THREADS, 0, st>>>(bpart.as<double>(), nblk_c, bdsum.as<double>());
+      cudaMemcpyAsync(tmp.data(), bdsum.as<double>(), sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      double cmin = 1.0;
+      for (int s = 0; s < nrhs; ++s)
+        cmin = std::min(cmin, tmp[s] / std::sqrt(std::max(rn2[s] * rn2[(size_t)k * nrhs + s], 1e-300)));
+      fprintf(stderr,
+              "bri refine: shift %d sigma %.4e  relres after phase 1 %.3e  |X|/|b| %.3e  cos(r_k, r_0) %.4f  (%s "
+              "residual)\n",
+              k, sig[k], worst, xmax, cmin, dw_slot[(size_t)k * nrhs] ? "double-word" : "FP64");
     }
   btmp1.reset();
   btmp2.reset();
@@ -978,16 +1213,23 @@ int refine_mixed(bri_ctx* c, const double* b, int nrhs, int n, const double* sig
         rn2[slot] = tmp[j];
         if (err_acc[slot] > 0.25 * goal && std::sqrt(rn2[slot]) <= goal) verify.push_back(slot);
       }
-      if (rlog) fprintf(stderr, "bri refine: round %d: %zu FP64 verifications\n", round, verify.size());
+      if (rlog) fprintf(stderr, "bri refine: round %d: %zu verification residuals\n", round, verify.size());
       if (!verify.empty()) {
         DevBuf v1, v2;
         if ((rc = v1.alloc(sizeof(double) * nreal, st))) return rc;
         if ((rc = v2.alloc(sizeof(double) * nreal, st))) return rc;
         for (int slot : verify) {
           const int k = slot / nrhs, sidx = slot % nrhs;
-          rc = residual64(c, m0, 1, b + (int64_t)sidx * nreal, X + (int64_t)slot * nreal, sig[k],
-                          bres.as<double>() + (int64_t)slot * nreal, v1.as<double>(), v2.as<double>(),
-                          bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+          // the solution has changed by a correction of ~1e-7 of its norm, so
+          // the phase-2 norm still decides the residual's arithmetic
+          if (dw_slot[slot])
+            rc = residual_dw(c, m0, 1, b + (int64_t)sidx * nreal, X + (int64_t)slot * nreal, sig[k],
+                             bres.as<double>() + (int64_t)slot * nreal, v1.as<double>(), v2.as<double>(),
+                             bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
+          else
+            rc = residual64(c, m0, 1, b + (int64_t)sidx * nreal, X + (int64_t)slot * nreal, sig[k],
+                            bres.as<double>() + (int64_t)slot * nreal, v1.as<double>(), v2.as<double>(),
+                            bpart.as<double>(), bdsum.as<double>(), tmp.data(), &cnt);
           if (rc) return rc;
           rn2[slot] = tmp[0];
           err_acc[slot] = 0.0;

@@ -70,6 +70,23 @@ def test_bri_apply_f64(dims, c_sw, dagger):
     assert relerr(y, want) < 1e-12
 
 
+@pytest.mark.parametrize("dims", [RAGGED, (4, 4, 4, 4)])
+@pytest.mark.parametrize("c_sw", [0.0, 1.0])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_bri_apply_double_word(dims, c_sw, dagger):
+    """The double-word FP32 operator (error-free transformations on the FP32 pipe) against the FP64
+    oracle: FP64-class accuracy, 1e-13 of the largest output element; a zero source stays zero."""
+    u = sf.gauge_field(dims, 11, 0.1, 3)
+    x = sf.gaussian_source(dims, 3, 1011)
+    x[1] = 0.0
+    lat = _lattice(dims, u, c_sw)
+    y = lat.bri_apply(torch.from_numpy(x).cuda(), -1.0, dagger=dagger, double_word=True).cpu().numpy()
+    op = dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=c_sw)
+    want = op.apply_dagger(x) if dagger else op.apply(x)
+    assert relerr(y, want) < 1e-13
+    assert np.abs(y[1]).max() == 0.0
+
+
 @pytest.mark.parametrize("bf16", [False, True])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_bri_apply_f32(bf16, dagger):
@@ -269,7 +286,8 @@ def _oracle_wilson_overlap():
     return want, swant1
 
 
-@pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "0,64,1", "1,64,1", "2,128,1", "2,64,1", "0,128,2", "0,128,4"])
+@pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "0,64,1", "1,64,1", "2,128,1", "2,64,1", "3,128,1",
+                                   "3,64,1", "0,128,2", "0,128,4"])
 def test_bri_apply_every_launch_configuration(force, monkeypatch):
     """Every stencil launch configuration the autotuner can pick gives the oracle's result
     (5 right-hand sides: groups plus a remainder)."""
@@ -283,6 +301,27 @@ def test_bri_apply_every_launch_configuration(force, monkeypatch):
         y = lat.bri_apply(torch.from_numpy(x).to(torch.complex64).cuda(), -1.0, dagger=dagger).cpu().numpy()
         want = op.apply_dagger(x) if dagger else op.apply(x)
         assert relerr(y, want) < 1e-5
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_sign_three_rhs():
+    u = sf.gauge_field(RAGGED, 10, 0.1, 3)
+    x = sf.gaussian_source(RAGGED, 3, 1019)
+    want, _ = overlap.sign_apply(dirac.DiracOperator(u, "bri", m0=-1.0, c_sw=1.0), x, 8, 1e-13)
+    return u, x, want
+
+
+@pytest.mark.parametrize("force", ["0,128,1", "1,128,1", "2,128,1", "2,64,1", "3,128,1", "3,64,1", "0,128,2"])
+def test_mixed_solve_every_launch_configuration(force, monkeypatch):
+    """The mixed-precision sign function with every stencil configuration forced (each D^dagger
+    launch of the FP32 solve carries the fused shift and dot-product epilogue; 3 right-hand sides:
+    a two-rhs group plus a remainder) matches the oracle within 1e-10."""
+    monkeypatch.setenv("BRI_STENCIL_FORCE", force)
+    u, x, want = _oracle_sign_three_rhs()
+    lat = _lattice(RAGGED, u, 1.0)
+    y, st = lat.sign_apply(torch.from_numpy(x).cuda(), n=8, rho=1.0, tol=1e-11, prec=PREC_F32)
+    assert st["converged"]
+    assert relerr(y.cpu().numpy(), want) < 1e-10
 
 
 def test_zero_source_and_free_field():
