@@ -79,7 +79,8 @@ typedef struct bri_ctx bri_ctx;
 typedef struct bri_stats {
   int iterations;          /* multi-shift CG iterations (max over rhs) */
   int matvecs;             /* applications of the kernel operator D or D^dagger */
-  int matvecs_f64;         /* of which in FP64 */
+  int matvecs_f64;         /* of which in FP64 (double-word FP32 applications count in
+                              matvecs only) */
   int refinements;         /* mixed precision: outer refinement rounds */
   int n_shifts;            /* number of shifts solved */
   double max_true_residual;/* max over rhs and shifts of ||b-(A+s_i)x_i||/||b|| (FP64),
@@ -88,7 +89,7 @@ typedef struct bri_stats {
   int want_true_residual;  /* input: compute FP64 true residuals per shift */
   int maxiter;             /* input: iteration cap (0 = default 20000) */
   double seconds;          /* wall time of the call */
-  double phase_seconds[4]; /* main multi-shift solve, FP64 residuals, corrections, final D */
+  double phase_seconds[4]; /* main multi-shift solve, FP64-class residuals, corrections, final D */
 } bri_stats;
 
 /* Create a context for one lattice.  dims: {Lx,Ly,Lz,Lt}, each >= 2.
@@ -144,8 +145,11 @@ int kl_coeffs(int n, int kind, double scale, double* c0, double* w, double* sigm
  * r(s) = c0 + sum_i w_i/(s+sigma_i) evaluated by one multi-shift CG
  * (Sec. 3.3, Sec. 4.1) to relative residual tol on every shift.
  * x, y: device complex128 [nrhs][V][4][3].  prec: BRI_PREC_F64 (all FP64) or
- * BRI_PREC_F32 / BRI_PREC_F32_BF16 (FP32 inner solve with FP32 or BF16 links,
- * FP64 reductions, FP64 defect-correction refinement to tol).  kind selects
+ * BRI_PREC_F32 / BRI_PREC_F32_BF16 (FP32 inner solve with FP32 or BF16 links
+ * and FP64-accumulated solutions, FP64 reductions, defect-correction refinement
+ * to tol on FP64-class residuals: the double-word FP32 operator of
+ * BRI_PREC_DW for the Brillouin kernel wherever its error bound, 1e-13 of the
+ * solution's norm, stays below 5 % of tol ||b||, else FP64).  kind selects
  * the Kenney-Laub family.  st may be NULL. */
 int sign_apply_multishift(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kind,
                           double rho, double scale, double tol, int prec, bri_stats* st);
@@ -165,7 +169,7 @@ int overlap_apply(bri_ctx* ctx, void* y, const void* x, int nrhs, int n, int kin
  * convergence flags of every system stay in device memory, and the iterations
  * run inside one CUDA graph whose conditional WHILE node repeats the
  * iteration until every system has converged (or reached the iteration cap),
- * with no host polling.  For the mixed precisions the FP64 residuals, FP32
+ * with no host polling.  For the mixed precisions the FP64-class residuals, FP32
  * corrections and the final application then run per lattice, concurrently
  * on the contexts' own streams.  At most 32 contexts, all on the current
  * device, each with the Brillouin kernel; ys[i], xs[i]: device complex128

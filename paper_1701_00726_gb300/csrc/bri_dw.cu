@@ -188,8 +188,9 @@ __device__ __forceinline__ void spin_apply(CDW y[4], const CDW x[4], float a, DW
 }
 
 // One thread per site and right-hand side (grid groups = right-hand sides, in
-// the order of stencil_grid).
-__global__ void __launch_bounds__(128, 2)
+// the order of stencil_grid).  One source colour at a time keeps 128
+// registers (16 warps per SM) without spills.
+__global__ void __launch_bounds__(128, 4)
     bri_kernel_dw(Geom g, float4* __restrict__ y, const float4* __restrict__ x, const float4* __restrict__ W,
                   const float2* __restrict__ cl, DW diag, float sgn, int gfirst, const __grid_constant__ HopTableDW H) {
   const int grp = gfirst ? blockIdx.x : blockIdx.y, blk = gfirst ? blockIdx.y : blockIdx.x;
@@ -231,50 +232,32 @@ __global__ void __launch_bounds__(128, 2)
     const float a = H.a[j];
     const DW c{sgn * H.ch[j], sgn * H.cl[j]};
     const DW cm{-c.h, -c.l};
-    // forward hop: acc += W_d(n) (M_d x(n+d))
-    {
-      CDW yv[4][3];
-#pragma unroll
+    // The two hops of the pair, one source colour b at a time (the spin matrix
+    // mixes spins only), as rolled loops so that the body fits the instruction
+    // cache:
+    //   forward  (h = 0): acc[.][aa] += W_d(n)[aa][b] (M_d x(n+d))[.][b]
+    //   backward (h = 1): acc[.][aa] += conj(W_d(n-d)[b][aa]) (M_{-d} x(n-d))[.][b]
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int m = h ? mm : mp;
+      const float4* wp = W + (int64_t)j * 9 * V + (h ? mm : n);
+      const DW ch = h ? cm : c;
+      const float cs = h ? -1.f : 1.f;  // conj(w) = (w_re, -w_im)
+#pragma unroll 1
       for (int b = 0; b < 3; ++b) {
         CDW xs[4], ys[4];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) xs[s] = ld_cdw(xin + (int64_t)mp * 12 + s * 3 + b);
-        spin_apply(ys, xs, a, c, d);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) yv[s][b] = ys[s];
-      }
-      const float4* wp = W + (int64_t)j * 9 * V + n;
-#pragma unroll
-      for (int aa = 0; aa < 3; ++aa)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const float4 w = __ldg(wp + (int64_t)(aa * 3 + b) * V);
-#pragma unroll
-          for (int s = 0; s < 4; ++s) cmac(acc[s][aa], w, yv[s][b]);
-        }
-    }
-    // backward hop: acc += W_d(n-d)^dagger (M_{-d} x(n-d))
-    {
-      CDW yv[4][3];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        CDW xs[4], ys[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) xs[s] = ld_cdw(xin + (int64_t)mm * 12 + s * 3 + b);
-        spin_apply(ys, xs, a, cm, d);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) yv[s][b] = ys[s];
-      }
-      const float4* wp = W + (int64_t)j * 9 * V + mm;
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
+        for (int s = 0; s < 4; ++s) xs[s] = ld_cdw(xin + (int64_t)m * 12 + s * 3 + b);
+        spin_apply(ys, xs, a, ch, d);
 #pragma unroll
         for (int aa = 0; aa < 3; ++aa) {
-          // (W^dagger)[aa][b] = conj(W[b][aa])
-          const float4 w = __ldg(wp + (int64_t)(b * 3 + aa) * V);
+          float4 w = __ldg(wp + (int64_t)(h ? b * 3 + aa : aa * 3 + b) * V);
+          w.z *= cs;
+          w.w *= cs;
 #pragma unroll
-          for (int s = 0; s < 4; ++s) cmac_cj(acc[s][aa], w, yv[s][b]);
+          for (int s = 0; s < 4; ++s) cmac(acc[s][aa], w, ys[s]);
         }
+      }
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s)
