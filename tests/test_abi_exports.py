@@ -35,3 +35,17 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
     # the Python binding covers the same names
     assert set(_declared()) <= set(_lib.EXPORTED)
+
+
+def test_binding_constants_match_the_header():
+    """Every integer #define of include/bri.h that the binding mirrors has the header's value."""
+    from paper_1701_00726_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "bri.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"^#define\s+BRI_([A-Z0-9_]+)\s+\(?(-?\d+)\)?", src, flags=re.M)}
+    mirrored = {"OK": "BRI_OK", "NOT_CONVERGED": "BRI_NOT_CONVERGED", "PREC_F64": "PREC_F64",
+                "PREC_F32": "PREC_F32", "PREC_F32_BF16": "PREC_F32_BF16", "PREC_DW": "PREC_DW",
+                "ANTIPERIODIC_T": "ANTIPERIODIC_T", "KERNEL_BRILLOUIN": "KERNEL_BRILLOUIN",
+                "KERNEL_WILSON": "KERNEL_WILSON", "KL_DIAGONAL": "KL_DIAGONAL", "KL_UPPER": "KL_UPPER",
+                "MAX_SHIFTS": "MAX_SHIFTS"}
+    for h, py in mirrored.items():
+        assert defs[h] == getattr(_lib, py), h
