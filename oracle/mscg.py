@@ -78,7 +78,8 @@ def multishift_cg(apply_a, b, sigmas, tol, maxiter=100000):
 
 
 def true_residuals(apply_a, b, sigmas, x):
-    """||b - (A + sigma_i) x_i|| / ||b|| for every shift."""
+    """||b - (A + sigma_i) x_i|| / ||b|| for every shift (the absolute norm for a zero source)."""
     bn = np.sqrt(vdot(b, b).real)
+    bn = bn if bn > 0.0 else 1.0
     return [np.sqrt(vdot(res, res).real) / bn
             for res in (b - apply_a(xi) - s * xi for xi, s in zip(x, sigmas))]
